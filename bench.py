@@ -1,0 +1,341 @@
+"""Throughput of the averaged-Yee field advance on GB300.
+
+Workload (one "step" = one full pass of the hot path: current filter, source,
+Algorithm 1, E update, Faraday update): a 2D periodic 4096 x 4096 grid, FP32
+storage (FP64 only in reductions), dt = 0.5 dt_CFL, random-phase field
+spectrum with power ~ |n|^-2 up to |n| = N/8, a static divergence-free
+current (curl of a smooth random potential, Gaussian spectrum of width 16
+cells) re-filtered by a 3-pass binomial filter every step, m = 4 sweeps.
+All inputs are seeded and synthetic.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank advances its own
+grid (independent replicas, weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX = NY = 4096
+M_SWEEPS = 4
+PASSES = 3
+COURANT = 0.5
+KMAX = NX // 8
+SEED = 1907002
+BYTES_PER_CELL = 15 * 4  # read E, B, j (9 x 4 B) + write E, B (6 x 4 B)
+METRIC = "Gcell-updates/s per full step (curl+iteration+filter) and % HBM roofline, 1 GB300"
+UNIT = "Gcell-updates/s"
+WORKLOAD = ("2D periodic 4096x4096 FP32 (FP64 reductions), dt=0.5 dt_CFL, power-law spectrum k_max=N/8, "
+            "static solenoidal J (curl of Gaussian-spectrum potential, width 16), 3-pass binomial current "
+            "filter every step, m=4 sweeps")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                d = json.load(f)
+            for key in ("hbm_gbs", "hbm_GBps", "hbm_bandwidth_gbs"):
+                if key in d and d[key]:
+                    return float(d[key]), f"measured ({key} of MEASURED_PEAKS.json)"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback (6.8 TB/s, no MEASURED_PEAKS.json)"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for name in ("fused2d.cu", "fused2d.h", "fmx_internal.h"):
+        with open(os.path.join(ROOT, "paper_1907_13088_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic():
+    """dram bytes per launch of the fused kernel from the committed ncu
+    summary, or None when absent or taken on another version of the kernel."""
+    path = os.path.join(ROOT, "profiles", "fused2d_4096_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("kernel_sha256_16") != _kernel_hash():
+            return None
+        return float(d["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 100 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [s for (t, s) in self.samples if t0 - 0.05 <= t <= t1 + 0.05] or [s for _, s in self.samples[-3:]]
+        if not rows:
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            parts = [p.strip() for p in r.split(",")]
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except Exception:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs():
+    import numpy as np
+    from paper_1907_13088_gb300 import synth
+    E, B = synth.power_law_fields((NX, NY), KMAX, SEED, dtype=np.float32)
+    J = synth.solenoidal_current((NX, NY), SEED + 1, width=16.0, rms=1e-3, dtype=np.float32)
+    return E, B, J
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_1907_13088_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1907_13088_gb300 import fmx
+
+    E, B, J = make_inputs()
+    g = fmx.Grid((NX, NY), precision=fmx.FMX_F32, m=M_SWEEPS, filter_passes=PASSES, courant=COURANT,
+                 engine=fmx.FMX_ENGINE_FUSED)
+    g.set_fields(E, B)
+    g.set_current(J)
+    stream = g.stream
+    cells = NX * NY
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # warm-up
+    g.step(args.warmup)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+        time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    l0 = g.launches
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    ev0.record(stream)
+    g.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    barrier()
+    launches = g.launches - l0
+    ms = ev0.elapsed_time(ev1)
+    t_rank = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_rank, op=dist.ReduceOp.MAX)
+    ms_max = float(t_rank.item())
+    clocks = sampler.summary(t0, t1) if rank == 0 else None
+    sampler.stop()
+
+    # end to end through the C ABI: every step uploads E, B, j from pinned
+    # host memory, advances one step, reads E, B back into pinned memory
+    e2e_steps = max(3, min(20, args.steps // 50))
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    hE, hB, hJ = pin(E), pin(B), pin(J)
+    hout = torch.empty((9, 1, NY, NX), dtype=torch.float32).pin_memory().numpy()
+    for _ in range(2):
+        g.set_fields(hE, hB)
+        g.set_current(hJ)
+        g.step(1)
+        g.get_fields(fmx.FMX_E | fmx.FMX_B, host_out=hout)
+    barrier()
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g.set_fields(hE, hB)
+        g.set_current(hJ)
+        g.step(1)
+        g.get_fields(fmx.FMX_E | fmx.FMX_B, host_out=hout)
+    torch.cuda.synchronize()
+    te1 = time.perf_counter()
+    e2e_s = torch.tensor([te1 - te0], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
+    e2e_value = world * cells * e2e_steps / float(e2e_s.item()) / 1e9
+
+    cpu = cpu_baseline() if (rank == 0 and args.cpu_baseline) else None
+
+    if rank == 0:
+        value = world * cells * args.steps / (ms_max / 1e3) / 1e9
+        per_launch_s = (ms / 1e3) / args.steps
+        achieved = BYTES_PER_CELL * cells / per_launch_s / 1e9
+        peak, peak_src = _peaks()
+        traffic = _ncu_traffic()
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 6), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [NX, NY], "cells_per_gpu": cells, "m": M_SWEEPS,
+                       "filter_passes": PASSES, "courant": COURANT, "engine": "fused2d",
+                       "l2": "inputs larger than L2 (1.0 GB of fields per step vs 129 MB L2)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "peak_source": peak_src, "bytes_per_cell_step": BYTES_PER_CELL,
+                         "kernel": "k_fused2d<float,4,3,true,256>"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": 9 * 4 * cells,
+                    "d2h_bytes_per_step": 6 * 4 * cells, "steps": e2e_steps,
+                    "path": "fmx_set_fields+fmx_set_current (pinned host) -> fmx_step(1) -> fmx_get_fields"},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _oracle_sample_rate(n, nsteps, threads):
+    """Runs the FP64 oracle on an n x n periodic sample of the workload;
+    returns (cell-updates/s, threads used, seconds)."""
+    import numpy as np
+    from oracle import core
+    from paper_1907_13088_gb300 import synth
+    used = core.threads(threads)
+    E, B = synth.power_law_fields((n, n), max(1, n // 8), SEED, dtype=np.float64)
+    J = synth.solenoidal_current((n, n), SEED + 1, width=16.0, rms=1e-3, dtype=np.float64)
+    p = core.Params(shape=(n, n), courant=COURANT, m=M_SWEEPS, filter_passes=PASSES, coef_f32=True)
+    t0 = time.perf_counter()
+    core.step(p, E, B, J, nsteps)
+    dt = time.perf_counter() - t0
+    return n * n * nsteps / dt, used, dt
+
+
+def cpu_baseline():
+    n, steps = 2048, 8
+    rate, used, secs = _oracle_sample_rate(n, steps, os.cpu_count() or 1)
+    return {"value": round(rate / 1e9, 6), "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"{n}x{n} periodic sample of the workload, {steps} steps, FP64 C oracle "
+                      f"({secs:.1f} s, OpenMP over rows)"}
+
+
+def run_reference(args):
+    rank, world, local = _dist()
+    if rank != 0:
+        return
+    from oracle import core
+    core.build()
+    threads = os.cpu_count() or 1
+    # size the per-step sample so the whole run stays within about two minutes
+    n = 256
+    rate, used, secs = _oracle_sample_rate(n, 1, threads)
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    while n > 32 and n * n / rate > budget:
+        n //= 2
+    _oracle_sample_rate(n, args.warmup, threads) if args.warmup else None
+    rate, used, secs = _oracle_sample_rate(n, args.steps, threads)
+    value = rate / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{n}x{n} periodic sample per step"},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": used, "kind": "oracle",
+                         "sample": f"{n}x{n} periodic sample of the workload per step, FP64 C oracle"},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

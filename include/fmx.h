@@ -1,0 +1,232 @@
+/*
+ * fmx.h -- C ABI of the GB300 field advance for the averaged-Yee (unlumped
+ * Eastwood finite-element) Maxwell scheme of Lu, Huang, Kilian, Guo, Li and
+ * Liang, "An O(N) Maxwell solver with improved numerical dispersion
+ * properties" (arXiv:1907.13088).
+ *
+ * One step advances the state (E^n, B^{n+1/2}) on a periodic staggered Yee
+ * grid to (E^{n+1}, B^{n+3/2}):
+ *   1. optional binomial low-pass filter of the current (Sec. 4.2, Sec. 5);
+ *   2. auxiliary-field source dE' = c dt curl(alpha B) - 4 pi dt j
+ *      (Eqs. ampere_aux_x..z);
+ *   3. Algorithm 1: dE_(0) = dE', dE_(s+1) = dE' + A dE_(s), with A from
+ *      Eqs. matrixA_1st..matrixA_last, either m sweeps or until a relative
+ *      residual target (Sec. 2.2.1 weighs both);
+ *   4. E^{n+1} = E^n + dE (Sec. 2.2.1);
+ *   5. B^{n+3/2} = B^{n+1/2} - c dt curl E^{n+1} (Eqs. faraday_x..z);
+ *   6. optional filter of the fields (Sec. 5, "post-process").
+ * 2D and 1D grids follow Secs. 2.2.2 and 2.2.3 (D -> 0, alpha -> 1 along the
+ * missing axes).  Units are Gaussian (4 pi / c), as in Eqs. ampere_x..z.
+ *
+ * Storage.  Every field component is its own device array, x fastest:
+ * element (i, j, k) at offset (k * n[1] + j) * pitch + i, i < n[0], with
+ * pitch >= n[0] and pitch * element size a multiple of 16 bytes, base
+ * address 16-byte aligned.  Index (i, j, k) of each component sits at its
+ * Yee position (Sec. 2 variable list):
+ *   Ex (i+1/2, j, k)   Ey (i, j+1/2, k)   Ez (i, j, k+1/2)
+ *   Bx (i, j+1/2, k+1/2)   By (i+1/2, j, k+1/2)   Bz (i+1/2, j+1/2, k)
+ * and the current colocated with E.  Boundaries are periodic.
+ *
+ * Ownership.  The caller allocates every device buffer (fields, their
+ * ping-pong partners, current, workspace) and keeps it alive until
+ * fmx_destroy; the library borrows them and never allocates or frees device
+ * memory.  Host memory passed to a call is only read or written during that
+ * call (copies are completed before the call returns when `where` is
+ * FMX_HOST).
+ *
+ * Errors.  Every entry point returns fmx_status (0 = FMX_OK) except
+ * fmx_destroy, fmx_strerror, fmx_last_error and the pure queries.  No C++
+ * exception crosses the ABI.  A failing call leaves a message in the
+ * calling thread's fmx_last_error().  Asynchronous calls (fmx_step,
+ * fmx_filter) only enqueue work on the grid's stream; a device-side
+ * failure surfaces at the next synchronising call (fmx_get_fields,
+ * fmx_diagnostics, fmx_sync).
+ */
+#ifndef FMX_H
+#define FMX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FMX_OK = 0,
+    FMX_EINVAL = 1,      /* an argument is out of range or inconsistent      */
+    FMX_ECFL = 2,        /* dt above dt_CFL (Eq. dt_cfl_3d and its 2D form)   */
+    FMX_ENOCONV = 3,     /* residual mode reached m_max sweeps unconverged    */
+    FMX_ECUDA = 4,       /* a CUDA runtime call failed                        */
+    FMX_ETIMEOUT = 5,    /* a bounded device-side wait gave up                */
+    FMX_ESTATE = 6,      /* call out of order (e.g. stepping before fmx_bind) */
+    FMX_EUNSUPPORTED = 7 /* combination this build does not provide           */
+} fmx_status;
+
+enum { FMX_F32 = 0, FMX_F64 = 1 };                        /* storage and sweep precision */
+enum { FMX_ITER_FIXED = 0, FMX_ITER_RESIDUAL = 1 };       /* Algorithm 1 stop rule       */
+enum { FMX_FILTER_NONE = 0, FMX_FILTER_CURRENT = 1, FMX_FILTER_FIELDS = 2 };
+enum { FMX_ENGINE_AUTO = 0, FMX_ENGINE_STAGED = 1, FMX_ENGINE_FUSED = 2 };
+enum { FMX_HOST = 0, FMX_DEVICE = 1 };                    /* where a copy source/target lives */
+
+/* component bits (index order of the pointer arrays below) */
+enum {
+    FMX_EX = 1 << 0, FMX_EY = 1 << 1, FMX_EZ = 1 << 2,
+    FMX_BX = 1 << 3, FMX_BY = 1 << 4, FMX_BZ = 1 << 5,
+    FMX_JX = 1 << 6, FMX_JY = 1 << 7, FMX_JZ = 1 << 8,
+    FMX_E = 7, FMX_B = 7 << 3, FMX_J = 7 << 6
+};
+
+/* warnings reported by fmx_create */
+enum {
+    FMX_WARN_ANORM = 1 /* 3D with dt > min(d)/(sqrt(2) c): the App. C bound
+                          ||A||_inf < 1 no longer guaranteed (Sec. 2.2.1) */
+};
+
+/* Number of coefficients returned by fmx_coefficients. */
+#define FMX_NCOEF 14
+
+typedef struct {
+    int dims;            /* active axes: 1 (x), 2 (x, y) or 3 (x, y, z)                  */
+    int64_t n[3];        /* cells per axis, >= 1; inactive axes must be 1               */
+    double d[3];         /* cell sizes (dx, dy, dz) > 0                                 */
+    double c;            /* speed of light > 0                                          */
+    double dt;           /* time step; if <= 0, dt = courant * dt_CFL                   */
+    double courant;      /* fraction of dt_CFL used when dt <= 0, in (0, 1]             */
+    int precision;       /* FMX_F32 or FMX_F64                                          */
+    int iter_mode;       /* FMX_ITER_FIXED or FMX_ITER_RESIDUAL                         */
+    int m;               /* sweeps of Algorithm 1 in fixed mode, >= 0                   */
+    double tol;          /* residual mode: stop when ||dE_(s+1)-dE_(s)|| <= tol ||dE'|| */
+    int m_max;           /* residual mode: sweep cap (FMX_ENOCONV beyond)               */
+    int filter_passes;   /* binomial (1/4,1/2,1/4) passes per active axis, >= 0         */
+    int filter_target;   /* FMX_FILTER_NONE / _CURRENT (each step, before the source) / _FIELDS (after the update) */
+    int lumped;          /* 1: alpha -> 1, A = 0 (the Yee scheme, Sec. 2)               */
+    int engine;          /* FMX_ENGINE_*: which kernels run the step                    */
+    int64_t pitch;       /* row pitch in elements; 0 = n[0] rounded up to 16 bytes      */
+    void *stream;        /* cudaStream_t the grid's work is enqueued on (NULL: legacy)  */
+} fmx_params;
+
+/* Device pointers the grid borrows (see Ownership).  E[s][c], B[s][c]:
+ * state set s in {0, 1}, component c in {x, y, z}.  Set 0 holds the state
+ * after fmx_set_fields; the fused engine alternates between the two sets,
+ * the staged engine works in place in the current set.  J[c] may be NULL
+ * (vacuum, j = 0).  work: fmx_workspace_bytes() bytes, 256-byte aligned. */
+typedef struct {
+    void *E[2][3];
+    void *B[2][3];
+    void *J[3];
+    void *work;
+    size_t work_bytes;
+} fmx_buffers;
+
+/* Diagnostics of the current state, accumulated in FP64 on the device. */
+typedef struct {
+    double w_scheme;    /* sum[E.(1-A)E + B^{n-1/2}.S B^{n+1/2}] dV/(8 pi): conserved by the converged vacuum step */
+    double w_plain;     /* sum[E^2 + B^2] dV/(8 pi)                                       */
+    double divb_max;    /* max |D.B| (Eq. gauss_B), cell centres                          */
+    double divb_l2;     /* sqrt(sum (D.B)^2)                                              */
+    double gauss_max;   /* max |D_x(alpha_yz Ex) + D_y(alpha_zx Ey) + D_z(alpha_xy Ez)| (Eq. gauss_E lhs) */
+    double gauss_l2;    /* its L2 norm                                                    */
+    double last_resid;  /* residual mode: relative residual of the last solve            */
+    int last_sweeps;    /* sweeps of the last solve                                       */
+    int64_t total_sweeps; /* sweeps since fmx_bind                                        */
+    int64_t steps;      /* steps since fmx_bind                                           */
+} fmx_diag;
+
+typedef struct fmx_grid fmx_grid;
+
+/* Validates p and creates a grid handle (host memory only; no device work).
+ * Computes dt (from courant when p->dt <= 0) and the coefficients.
+ * *warnings receives FMX_WARN_* bits (may be NULL).
+ * Errors: FMX_EINVAL (bad sizes, dims, precision, modes, pitch),
+ * FMX_ECFL (dt > dt_CFL, Eq. dt_cfl_3d), FMX_EUNSUPPORTED (engine FUSED
+ * requested for a case the fused kernel does not cover). */
+fmx_status fmx_create(const fmx_params *p, fmx_grid **out, int *warnings);
+
+/* Bytes of one field-component array: pitch * n[1] * n[2] * element size.
+ * Returns 0 if p is invalid. */
+size_t fmx_field_bytes(const fmx_params *p);
+
+/* Bytes of workspace fmx_bind needs (intermediates of the staged engine,
+ * FP64 reduction partials, the device status block).  0 if p is invalid. */
+size_t fmx_workspace_bytes(const fmx_params *p);
+
+/* Lends the grid its device buffers (see fmx_buffers).  Checks alignment
+ * (16 bytes for fields, 256 for work) and work_bytes.  Resets the step and
+ * sweep counters and selects state set 0.  Errors: FMX_EINVAL. */
+fmx_status fmx_bind(fmx_grid *g, const fmx_buffers *b);
+
+/* Copies the components in `mask` (FMX_E/FMX_B bits) from src[c] (c = 0..5:
+ * Ex, Ey, Ez, Bx, By, Bz; entries outside mask ignored) into the current
+ * state set.  Sources are dense (pitch = n[0]) arrays of the grid's
+ * precision; `where` says whether they are host or device memory.  E is
+ * read as E^n and B as B^{n+1/2}.  Host copies complete before return;
+ * device copies are enqueued on the stream.  Errors: FMX_EINVAL,
+ * FMX_ESTATE (not bound), FMX_ECUDA. */
+fmx_status fmx_set_fields(fmx_grid *g, unsigned mask, const void *const *src, int where);
+
+/* Copies the current j^{n+1/2} (three dense arrays, x, y, z) into the
+ * bound J buffers, which are then used unchanged by every following step
+ * until the next call.  Errors as fmx_set_fields; FMX_ESTATE if J buffers
+ * were bound as NULL. */
+fmx_status fmx_set_current(fmx_grid *g, const void *const *src, int where);
+
+/* Enqueues nsteps full steps (1..6 above) on the stream.  Fixed mode never
+ * synchronises.  Residual mode reads the device residual back every few
+ * sweeps (synchronising) and returns FMX_ENOCONV if a solve reaches m_max.
+ * Errors: FMX_ESTATE, FMX_EINVAL (nsteps < 0), FMX_ECUDA, FMX_ENOCONV. */
+fmx_status fmx_step(fmx_grid *g, int nsteps);
+
+/* Applies `passes` binomial passes along every active axis to the
+ * components in mask (FMX_E, FMX_B, FMX_J bits), in place on the current
+ * state -- the "post-process the fields and currents" option of Sec. 5.
+ * Enqueued on the stream.  Errors: FMX_ESTATE, FMX_EINVAL. */
+fmx_status fmx_filter(fmx_grid *g, unsigned mask, int passes);
+
+/* Copies the components in mask (FMX_E/FMX_B/FMX_J bits; dst indexed
+ * 0..8 as Ex..Bz, Jx, Jy, Jz) out of the current state into dense arrays at
+ * dst[c].  Synchronises the stream.  Errors: FMX_EINVAL, FMX_ESTATE,
+ * FMX_ECUDA, FMX_ETIMEOUT (a latched device status). */
+fmx_status fmx_get_fields(fmx_grid *g, unsigned mask, void *const *dst, int where);
+
+/* Computes the FP64 diagnostics of the current state.  Synchronises.
+ * Errors: FMX_ESTATE, FMX_ECUDA. */
+fmx_status fmx_diagnostics(fmx_grid *g, fmx_diag *out);
+
+/* Waits for the grid's stream and returns any latched device status. */
+fmx_status fmx_sync(fmx_grid *g);
+
+/* The FMX_NCOEF scalar factors the kernels multiply by, after rounding to
+ * the grid's precision, as doubles, in this order: c dt/dx, c dt/dy,
+ * c dt/dz, 4 pi dt, 1/6 (alpha = 1 + Dbar^2/6), (sigma_x - 1)/6,
+ * (sigma_y - 1)/6, (sigma_z - 1)/6, (sigma_y + sigma_z - 1)/36,
+ * (sigma_z + sigma_x - 1)/36, (sigma_x + sigma_y - 1)/36, -sigma_yz/6,
+ * -sigma_zx/6, -sigma_xy/6; sigma_i = (c dt/d_i)^2, sigma_ij = (c dt/d_i)
+ * (c dt/d_j), each evaluated in binary64 in the order written, then
+ * rounded once (Eqs. matrixA_1st..matrixA_last).  Lumped grids report 0
+ * for entries 4..13.  Host-only; returns FMX_EINVAL if n < FMX_NCOEF. */
+fmx_status fmx_coefficients(const fmx_grid *g, double *out, int n);
+
+/* dt in use (after courant * dt_CFL). */
+double fmx_time_step(const fmx_grid *g);
+
+/* Device pointer of component c (0..5: Ex..Bz of the current state set,
+ * 6..8: Jx..Jz), or NULL. */
+void *fmx_field_ptr(const fmx_grid *g, int c);
+
+/* Number of device kernels this grid has launched since fmx_bind. */
+int64_t fmx_launch_count(const fmx_grid *g);
+
+/* Releases the handle (host memory only; borrowed buffers are untouched). */
+void fmx_destroy(fmx_grid *g);
+
+/* Static description of a status code. */
+const char *fmx_strerror(fmx_status s);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *fmx_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMX_H */

@@ -1,0 +1,632 @@
+// Host side of the C ABI declared in include/fmx.h: parameter validation,
+// the scheme's coefficients, buffer binding, copies, and the dispatch of a
+// step to the staged or fused kernels.  No device memory is allocated here:
+// every device buffer is borrowed from the caller.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "fmx.h"
+#include "fmx_internal.h"
+#include "fused2d.h"
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+fmx_status fail(fmx_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+fmx_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(FMX_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+double dt_cfl(const fmx_params *p) {
+    double s = 0.0;
+    for (int a = 0; a < p->dims; ++a) s += 1.0 / (p->d[a] * p->d[a]);
+    return 1.0 / (p->c * sqrt(s));
+}
+
+size_t elem_size(int precision) { return precision == FMX_F64 ? 8 : 4; }
+
+int64_t pitch_of(const fmx_params *p) {
+    if (p->pitch > 0) return p->pitch;
+    const int64_t q = (int64_t)(16 / elem_size(p->precision));
+    return (p->n[0] + q - 1) / q * q;
+}
+
+// Which engine runs a step of this problem.
+int resolve_engine(const fmx_params *p) {
+    const bool fusable = fmx::fused2d_supported(p);
+    if (p->engine == FMX_ENGINE_FUSED) return fusable ? FMX_ENGINE_FUSED : -1;
+    if (p->engine == FMX_ENGINE_STAGED) return FMX_ENGINE_STAGED;
+    return fusable ? FMX_ENGINE_FUSED : FMX_ENGINE_STAGED;
+}
+
+fmx_status validate(const fmx_params *p, double *dt_out, int *warn) {
+    if (!p) return fail(FMX_EINVAL, "params is NULL");
+    if (p->dims < 1 || p->dims > 3) return fail(FMX_EINVAL, "dims must be 1, 2 or 3 (got %d)", p->dims);
+    for (int a = 0; a < 3; ++a) {
+        if (p->n[a] < 1 || p->n[a] > (int64_t)1 << 30) return fail(FMX_EINVAL, "n[%d] out of range", a);
+        if (a >= p->dims && p->n[a] != 1) return fail(FMX_EINVAL, "inactive axis %d must have n = 1", a);
+        if (a < p->dims && !(p->d[a] > 0.0)) return fail(FMX_EINVAL, "d[%d] must be > 0", a);
+    }
+    if (!(p->c > 0.0)) return fail(FMX_EINVAL, "c must be > 0");
+    if (p->precision != FMX_F32 && p->precision != FMX_F64) return fail(FMX_EINVAL, "bad precision");
+    if (p->iter_mode != FMX_ITER_FIXED && p->iter_mode != FMX_ITER_RESIDUAL) return fail(FMX_EINVAL, "bad iter_mode");
+    if (p->iter_mode == FMX_ITER_FIXED && (p->m < 0 || p->m > 1 << 20)) return fail(FMX_EINVAL, "m out of range");
+    if (p->iter_mode == FMX_ITER_RESIDUAL && (!(p->tol > 0.0) || p->m_max < 1))
+        return fail(FMX_EINVAL, "residual mode needs tol > 0 and m_max >= 1");
+    if (p->filter_passes < 0 || p->filter_passes > 1024) return fail(FMX_EINVAL, "filter_passes out of range");
+    if (p->filter_target < FMX_FILTER_NONE || p->filter_target > FMX_FILTER_FIELDS)
+        return fail(FMX_EINVAL, "bad filter_target");
+    if (p->engine < FMX_ENGINE_AUTO || p->engine > FMX_ENGINE_FUSED) return fail(FMX_EINVAL, "bad engine");
+    const int64_t q = (int64_t)(16 / elem_size(p->precision));
+    if (p->pitch != 0 && (p->pitch < p->n[0] || p->pitch % q != 0))
+        return fail(FMX_EINVAL, "pitch must be >= n[0] and a multiple of 16 bytes");
+    const double cfl = dt_cfl(p);
+    double dt = p->dt;
+    if (!(dt > 0.0)) {
+        if (!(p->courant > 0.0)) return fail(FMX_EINVAL, "need dt > 0 or courant > 0");
+        dt = p->courant * cfl;
+    }
+    // Eq. dt_cfl_3d: real omega needs c dt <= (sum 1/d_i^2)^(-1/2)
+    if (dt > cfl * (1.0 + 1e-12)) return fail(FMX_ECFL, "dt %.17g above dt_CFL %.17g", dt, cfl);
+    int w = 0;
+    if (p->dims == 3 && !p->lumped) {
+        double dmin = p->d[0];
+        for (int a = 1; a < 3; ++a) dmin = p->d[a] < dmin ? p->d[a] : dmin;
+        if (p->c * dt > dmin / sqrt(2.0)) w |= FMX_WARN_ANORM;  // App. C bound, 3D
+    }
+    if (resolve_engine(p) < 0) return fail(FMX_EUNSUPPORTED, "the fused engine does not cover this problem");
+    *dt_out = dt;
+    if (warn) *warn = w;
+    return FMX_OK;
+}
+
+// The scalar factors of the step, in the order and with the expressions
+// documented at fmx_coefficients, evaluated in binary64 (this file is built
+// without floating-point contraction) and rounded once to the precision.
+void coefficients(const fmx_params *p, double dt, double co[FMX_NCOEF]) {
+    const double cdt = p->c * dt;
+    double k[3], s[3];
+    for (int a = 0; a < 3; ++a) {
+        k[a] = cdt / p->d[a];
+        s[a] = k[a] * k[a];
+    }
+    co[0] = k[0];
+    co[1] = k[1];
+    co[2] = k[2];
+    co[3] = (4.0 * M_PI) * dt;
+    if (p->lumped) {
+        for (int c = 4; c < FMX_NCOEF; ++c) co[c] = 0.0;
+    } else {
+        co[4] = 1.0 / 6.0;
+        co[5] = (s[0] - 1.0) / 6.0;
+        co[6] = (s[1] - 1.0) / 6.0;
+        co[7] = (s[2] - 1.0) / 6.0;
+        co[8] = (s[1] + s[2] - 1.0) / 36.0;
+        co[9] = (s[2] + s[0] - 1.0) / 36.0;
+        co[10] = (s[0] + s[1] - 1.0) / 36.0;
+        co[11] = -(k[1] * k[2]) / 6.0;
+        co[12] = -(k[2] * k[0]) / 6.0;
+        co[13] = -(k[0] * k[1]) / 6.0;
+    }
+    if (p->precision == FMX_F32)
+        for (int c = 0; c < FMX_NCOEF; ++c) co[c] = (double)(float)co[c];
+}
+
+template <typename T>
+fmx::Coef<T> make_coef(const double co[FMX_NCOEF]) {
+    fmx::Coef<T> c;
+    c.kx = (T)co[0];
+    c.ky = (T)co[1];
+    c.kz = (T)co[2];
+    c.q = (T)co[3];
+    c.c6 = (T)co[4];
+    c.ax = (T)co[5];
+    c.ay = (T)co[6];
+    c.az = (T)co[7];
+    c.ayz = (T)co[8];
+    c.azx = (T)co[9];
+    c.axy = (T)co[10];
+    c.byz = (T)co[11];
+    c.bzx = (T)co[12];
+    c.bxy = (T)co[13];
+    return c;
+}
+
+}  // namespace
+
+struct fmx_grid {
+    fmx_params p;
+    double dt = 0.0;
+    double co[FMX_NCOEF];
+    int engine = FMX_ENGINE_STAGED;
+    fmx::Geo geo;
+    size_t elem = 4;
+    size_t field_bytes = 0;
+    bool bound = false;
+    fmx_buffers buf;
+    int cur = 0;
+    cudaStream_t stream = nullptr;
+    // workspace carve
+    void *jf[3] = {nullptr, nullptr, nullptr};
+    void *tmp = nullptr;
+    void *dEp[3] = {nullptr, nullptr, nullptr};
+    void *dEa[3] = {nullptr, nullptr, nullptr};
+    void *dEb[3] = {nullptr, nullptr, nullptr};
+    double *partials = nullptr;
+    int64_t nparts = 0;
+    double *diag_out = nullptr;
+    fmx::DevStatus *st = nullptr;
+    // counters
+    int64_t steps = 0, total_sweeps = 0, launches = 0;
+    int last_sweeps = 0;
+    double last_resid = 0.0;
+};
+
+namespace {
+
+int staged_arrays(int engine) { return engine == FMX_ENGINE_STAGED ? 13 : 1; }
+
+fmx::Geo geo_of(const fmx_params *p) {
+    fmx::Geo g;
+    g.nx = (int)p->n[0];
+    g.ny = (int)p->n[1];
+    g.nz = (int)p->n[2];
+    g.pitch = pitch_of(p);
+    g.plane = g.pitch * p->n[1];
+    return g;
+}
+
+size_t workspace_of(const fmx_params *p, int engine) {
+    const fmx::Geo g = geo_of(p);
+    const size_t fb = align_up((size_t)g.plane * (size_t)g.nz * elem_size(p->precision), kAlign);
+    const int64_t slots = fmx::staged_partial_slots(g);
+    size_t w = (size_t)staged_arrays(engine) * fb;
+    w += align_up((size_t)slots * 8 * sizeof(double), kAlign);
+    w += align_up(8 * sizeof(double), kAlign);
+    w += align_up(sizeof(fmx::DevStatus), kAlign);
+    return w;
+}
+
+fmx_status check_launch(fmx_grid *g, const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    (void)g;
+    return FMX_OK;
+}
+
+template <typename T>
+fmx::StagedPtrs<T> staged_ptrs(fmx_grid *g) {
+    fmx::StagedPtrs<T> P;
+    for (int c = 0; c < 3; ++c) {
+        P.E[c] = (T *)g->buf.E[g->cur][c];
+        P.B[c] = (T *)g->buf.B[g->cur][c];
+        P.J[c] = (const T *)g->buf.J[c];
+        P.jf[c] = (T *)g->jf[c];
+        P.dEp[c] = (T *)g->dEp[c];
+        P.dEa[c] = (T *)g->dEa[c];
+        P.dEb[c] = (T *)g->dEb[c];
+    }
+    P.tmp = (T *)g->tmp;
+    P.partials = g->partials;
+    P.st = g->st;
+    return P;
+}
+
+// `passes` binomial passes along every active axis of one component, in
+// place on f, ping-ponging with the tmp scratch array.
+template <typename T>
+fmx_status filter_in_place(fmx_grid *g, T *f, int passes) {
+    const int n = passes * g->p.dims;
+    if (n == 0) return FMX_OK;
+    T *tmp = (T *)g->tmp;
+    const T *src = f;
+    for (int q = 0; q < n; ++q) {
+        T *dst = (q % 2 == 0) ? tmp : f;
+        g->launches += fmx::launch_filter_pass<T>(g->geo, g->p.dims, src, dst, q % g->p.dims, g->stream);
+        src = dst;
+    }
+    if (src != f) {
+        cudaError_t e = cudaMemcpyAsync(f, src, g->field_bytes, cudaMemcpyDeviceToDevice, g->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (filter)");
+    }
+    return check_launch(g, "filter kernel launch");
+}
+
+// Filters the current into the jf workspace (out of place; J is unchanged)
+// and returns in jsrc the arrays the source stage should read.
+template <typename T>
+fmx_status filtered_current(fmx_grid *g, const T *jsrc[3]) {
+    const bool have_j = g->buf.J[0] != nullptr;
+    for (int c = 0; c < 3; ++c) jsrc[c] = have_j ? (const T *)g->buf.J[c] : nullptr;
+    if (!have_j || g->p.filter_target != FMX_FILTER_CURRENT || g->p.filter_passes == 0) return FMX_OK;
+    const int n = g->p.filter_passes * g->p.dims;
+    for (int c = 0; c < 3; ++c) {
+        const T *src = (const T *)g->buf.J[c];
+        T *jf = (T *)g->jf[c];
+        T *tmp = (T *)g->tmp;
+        for (int q = 0; q < n; ++q) {
+            // choose the first target so that the last pass lands in jf
+            T *dst = ((n - 1 - q) % 2 == 0) ? jf : tmp;
+            g->launches += fmx::launch_filter_pass<T>(g->geo, g->p.dims, src, dst, q % g->p.dims, g->stream);
+            src = dst;
+        }
+        jsrc[c] = jf;
+    }
+    return check_launch(g, "current filter launch");
+}
+
+template <typename T>
+fmx_status staged_step(fmx_grid *g) {
+    const fmx::Coef<T> c = make_coef<T>(g->co);
+    fmx::StagedPtrs<T> P = staged_ptrs<T>(g);
+    const T *jsrc[3];
+    fmx_status s = filtered_current<T>(g, jsrc);
+    if (s != FMX_OK) return s;
+    const bool resid = g->p.iter_mode == FMX_ITER_RESIDUAL;
+    g->launches += fmx::launch_staged_source<T>(g->geo, g->p.dims, c, P, jsrc, g->stream, resid);
+    if (!resid) {
+        const T *in[3] = {P.dEp[0], P.dEp[1], P.dEp[2]};
+        for (int it = 0; it < g->p.m; ++it) {
+            T *out[3];
+            for (int q = 0; q < 3; ++q) out[q] = (it % 2 == 0) ? P.dEa[q] : P.dEb[q];
+            g->launches += fmx::launch_staged_sweep<T>(g->geo, g->p.dims, c, P, in, out, false, g->stream);
+            for (int q = 0; q < 3; ++q) in[q] = out[q];
+        }
+        g->launches += fmx::launch_update_e<T>(g->geo, P.E, in, g->stream);
+        g->last_sweeps = g->p.m;
+        g->total_sweeps += g->p.m;
+    } else {
+        g->launches += fmx::launch_resid_init(g->partials, g->nparts, g->st, g->stream);
+        fmx::DevStatus hs;
+        const double tol2 = g->p.tol * g->p.tol;
+        for (;;) {
+            for (int q = 0; q < 8; ++q) {
+                g->launches += fmx::launch_resid_sweep<T>(g->geo, g->p.dims, c, P, g->stream);
+                g->launches += fmx::launch_resid_update(g->partials, g->nparts, g->st, tol2, g->p.m_max, g->stream);
+            }
+            s = check_launch(g, "residual sweep launch");
+            if (s != FMX_OK) return s;
+            cudaError_t e = cudaMemcpyAsync(&hs, g->st, sizeof(hs), cudaMemcpyDeviceToHost, g->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "residual status read-back");
+            if (hs.done) break;
+        }
+        g->launches += fmx::launch_update_e_resid<T>(g->geo, P, g->stream);
+        g->last_sweeps = hs.count;
+        g->total_sweeps += hs.count;
+        g->last_resid = hs.nrm2 > 0.0 ? sqrt(hs.r2 / hs.nrm2) : 0.0;
+        if (hs.noconv) {
+            g->launches += fmx::launch_faraday<T>(g->geo, g->p.dims, c, P.E, P.B, g->stream);
+            return fail(FMX_ENOCONV, "residual %.3g above tol after %d sweeps", g->last_resid, hs.count);
+        }
+    }
+    g->launches += fmx::launch_faraday<T>(g->geo, g->p.dims, c, P.E, P.B, g->stream);
+    s = check_launch(g, "staged step launch");
+    if (s != FMX_OK) return s;
+    if (g->p.filter_target == FMX_FILTER_FIELDS && g->p.filter_passes > 0) {
+        for (int q = 0; q < 3; ++q) {
+            if ((s = filter_in_place<T>(g, P.E[q], g->p.filter_passes)) != FMX_OK) return s;
+            if ((s = filter_in_place<T>(g, P.B[q], g->p.filter_passes)) != FMX_OK) return s;
+        }
+    }
+    return FMX_OK;
+}
+
+template <typename T>
+fmx_status fused_step(fmx_grid *g, int nsteps) {
+    const fmx::Coef<T> c = make_coef<T>(g->co);
+    for (int n = 0; n < nsteps; ++n) {
+        const int nxt = 1 - g->cur;
+        fmx::Fused2dArgs<T> a;
+        for (int q = 0; q < 3; ++q) {
+            a.E[q] = (const T *)g->buf.E[g->cur][q];
+            a.B[q] = (const T *)g->buf.B[g->cur][q];
+            a.J[q] = (const T *)g->buf.J[q];
+            a.Eo[q] = (T *)g->buf.E[nxt][q];
+            a.Bo[q] = (T *)g->buf.B[nxt][q];
+        }
+        a.m = g->p.m;
+        a.passes = (g->p.filter_target == FMX_FILTER_CURRENT && g->buf.J[0]) ? g->p.filter_passes : 0;
+        int nl = fmx::launch_fused2d<T>(g->geo, c, a, g->stream);
+        if (nl < 0) return fail(FMX_EUNSUPPORTED, "fused 2D kernel: configuration not instantiated");
+        g->launches += nl;
+        g->cur = nxt;
+        g->last_sweeps = g->p.m;
+        g->total_sweeps += g->p.m;
+    }
+    return check_launch(g, "fused step launch");
+}
+
+fmx_status copy_rows(fmx_grid *g, void *dst, size_t dpitch, const void *src, size_t spitch, bool sync) {
+    const size_t width = (size_t)g->geo.nx * g->elem;
+    const size_t rows = (size_t)g->geo.ny * (size_t)g->geo.nz;
+    cudaError_t e = cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, rows, cudaMemcpyDefault, g->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2DAsync");
+    if (sync) {
+        e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    }
+    return FMX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fmx_status fmx_create(const fmx_params *p, fmx_grid **out, int *warnings) {
+    if (!out) return fail(FMX_EINVAL, "out is NULL");
+    *out = nullptr;
+    double dt = 0.0;
+    fmx_status s = validate(p, &dt, warnings);
+    if (s != FMX_OK) return s;
+    fmx_grid *g = new (std::nothrow) fmx_grid;
+    if (!g) return fail(FMX_EINVAL, "out of host memory");
+    g->p = *p;
+    g->dt = dt;
+    coefficients(p, dt, g->co);
+    g->engine = resolve_engine(p);
+    g->geo = geo_of(p);
+    g->elem = elem_size(p->precision);
+    g->field_bytes = (size_t)g->geo.plane * (size_t)g->geo.nz * g->elem;
+    g->stream = (cudaStream_t)p->stream;
+    memset(&g->buf, 0, sizeof(g->buf));
+    *out = g;
+    return FMX_OK;
+}
+
+size_t fmx_field_bytes(const fmx_params *p) {
+    double dt;
+    if (validate(p, &dt, nullptr) != FMX_OK) return 0;
+    const fmx::Geo g = geo_of(p);
+    return (size_t)g.plane * (size_t)g.nz * elem_size(p->precision);
+}
+
+size_t fmx_workspace_bytes(const fmx_params *p) {
+    double dt;
+    if (validate(p, &dt, nullptr) != FMX_OK) return 0;
+    return workspace_of(p, resolve_engine(p));
+}
+
+fmx_status fmx_bind(fmx_grid *g, const fmx_buffers *b) {
+    if (!g || !b) return fail(FMX_EINVAL, "NULL argument");
+    for (int s = 0; s < 2; ++s)
+        for (int c = 0; c < 3; ++c) {
+            const void *e = b->E[s][c], *bb = b->B[s][c];
+            const bool need = s == 0 || g->engine == FMX_ENGINE_FUSED;
+            if (need && (!e || !bb)) return fail(FMX_EINVAL, "state set %d component %d is NULL", s, c);
+            if (((uintptr_t)e | (uintptr_t)bb) % 16) return fail(FMX_EINVAL, "field buffers must be 16-byte aligned");
+        }
+    const bool any_j = b->J[0] || b->J[1] || b->J[2];
+    if (any_j && !(b->J[0] && b->J[1] && b->J[2])) return fail(FMX_EINVAL, "bind all three J buffers or none");
+    for (int c = 0; c < 3; ++c)
+        if ((uintptr_t)b->J[c] % 16) return fail(FMX_EINVAL, "J buffers must be 16-byte aligned");
+    const size_t need = workspace_of(&g->p, g->engine);
+    if (!b->work || b->work_bytes < need)
+        return fail(FMX_EINVAL, "workspace of %zu bytes needed (got %zu)", need, b->work_bytes);
+    if ((uintptr_t)b->work % kAlign) return fail(FMX_EINVAL, "workspace must be 256-byte aligned");
+    g->buf = *b;
+    char *w = (char *)b->work;
+    const size_t fb = align_up(g->field_bytes, kAlign);
+    if (g->engine == FMX_ENGINE_STAGED) {
+        for (int c = 0; c < 3; ++c) { g->jf[c] = w; w += fb; }
+        g->tmp = w; w += fb;
+        for (int c = 0; c < 3; ++c) { g->dEp[c] = w; w += fb; }
+        for (int c = 0; c < 3; ++c) { g->dEa[c] = w; w += fb; }
+        for (int c = 0; c < 3; ++c) { g->dEb[c] = w; w += fb; }
+    } else {
+        g->tmp = w; w += fb;
+    }
+    const int64_t slots = fmx::staged_partial_slots(g->geo);
+    g->partials = (double *)w;
+    g->nparts = slots * 8;
+    w += align_up((size_t)slots * 8 * sizeof(double), kAlign);
+    g->diag_out = (double *)w;
+    w += align_up(8 * sizeof(double), kAlign);
+    g->st = (fmx::DevStatus *)w;
+    // status partials count for the residual reductions is one per block
+    g->nparts = slots;
+    cudaError_t e = cudaMemsetAsync(g->st, 0, sizeof(fmx::DevStatus), g->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (status)");
+    g->cur = 0;
+    g->steps = g->total_sweeps = g->launches = 0;
+    g->last_sweeps = 0;
+    g->last_resid = 0.0;
+    g->bound = true;
+    return FMX_OK;
+}
+
+fmx_status fmx_set_fields(fmx_grid *g, unsigned mask, const void *const *src, int where) {
+    if (!g || !src) return fail(FMX_EINVAL, "NULL argument");
+    if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
+    if (mask & ~(unsigned)(FMX_E | FMX_B)) return fail(FMX_EINVAL, "mask holds bits other than E and B");
+    const size_t sp = (size_t)g->geo.nx * g->elem, dp = (size_t)g->geo.pitch * g->elem;
+    for (int c = 0; c < 6; ++c) {
+        if (!(mask & (1u << c))) continue;
+        if (!src[c]) return fail(FMX_EINVAL, "src[%d] is NULL", c);
+        void *dst = c < 3 ? g->buf.E[g->cur][c] : g->buf.B[g->cur][c - 3];
+        fmx_status s = copy_rows(g, dst, dp, src[c], sp, false);
+        if (s != FMX_OK) return s;
+    }
+    if (where == FMX_HOST) {
+        cudaError_t e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    }
+    return FMX_OK;
+}
+
+fmx_status fmx_set_current(fmx_grid *g, const void *const *src, int where) {
+    if (!g || !src) return fail(FMX_EINVAL, "NULL argument");
+    if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
+    if (!g->buf.J[0]) return fail(FMX_ESTATE, "no J buffers bound");
+    const size_t sp = (size_t)g->geo.nx * g->elem, dp = (size_t)g->geo.pitch * g->elem;
+    for (int c = 0; c < 3; ++c) {
+        if (!src[c]) return fail(FMX_EINVAL, "src[%d] is NULL", c);
+        fmx_status s = copy_rows(g, g->buf.J[c], dp, src[c], sp, false);
+        if (s != FMX_OK) return s;
+    }
+    if (where == FMX_HOST) {
+        cudaError_t e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    }
+    return FMX_OK;
+}
+
+fmx_status fmx_step(fmx_grid *g, int nsteps) {
+    if (!g) return fail(FMX_EINVAL, "NULL grid");
+    if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
+    if (nsteps < 0) return fail(FMX_EINVAL, "nsteps < 0");
+    if (g->engine == FMX_ENGINE_FUSED) {
+        fmx_status s = g->p.precision == FMX_F64 ? fused_step<double>(g, nsteps) : fused_step<float>(g, nsteps);
+        if (s == FMX_OK) g->steps += nsteps;
+        return s;
+    }
+    for (int n = 0; n < nsteps; ++n) {
+        fmx_status s = g->p.precision == FMX_F64 ? staged_step<double>(g) : staged_step<float>(g);
+        if (s != FMX_OK) return s;
+        g->steps += 1;
+    }
+    return FMX_OK;
+}
+
+fmx_status fmx_filter(fmx_grid *g, unsigned mask, int passes) {
+    if (!g) return fail(FMX_EINVAL, "NULL grid");
+    if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
+    if (passes < 0) return fail(FMX_EINVAL, "passes < 0");
+    if (mask & ~(unsigned)(FMX_E | FMX_B | FMX_J)) return fail(FMX_EINVAL, "bad mask");
+    if ((mask & FMX_J) && !g->buf.J[0]) return fail(FMX_ESTATE, "no J buffers bound");
+    for (int c = 0; c < 9; ++c) {
+        if (!(mask & (1u << c))) continue;
+        void *f = c < 3 ? g->buf.E[g->cur][c] : (c < 6 ? g->buf.B[g->cur][c - 3] : g->buf.J[c - 6]);
+        fmx_status s = g->p.precision == FMX_F64 ? filter_in_place<double>(g, (double *)f, passes)
+                                                 : filter_in_place<float>(g, (float *)f, passes);
+        if (s != FMX_OK) return s;
+    }
+    return FMX_OK;
+}
+
+fmx_status fmx_get_fields(fmx_grid *g, unsigned mask, void *const *dst, int where) {
+    if (!g || !dst) return fail(FMX_EINVAL, "NULL argument");
+    if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
+    if (mask & ~(unsigned)(FMX_E | FMX_B | FMX_J)) return fail(FMX_EINVAL, "bad mask");
+    if ((mask & FMX_J) && !g->buf.J[0]) return fail(FMX_ESTATE, "no J buffers bound");
+    (void)where;
+    const size_t dp = (size_t)g->geo.nx * g->elem, sp = (size_t)g->geo.pitch * g->elem;
+    for (int c = 0; c < 9; ++c) {
+        if (!(mask & (1u << c))) continue;
+        if (!dst[c]) return fail(FMX_EINVAL, "dst[%d] is NULL", c);
+        const void *f = c < 3 ? g->buf.E[g->cur][c] : (c < 6 ? g->buf.B[g->cur][c - 3] : g->buf.J[c - 6]);
+        fmx_status s = copy_rows(g, dst[c], dp, f, sp, false);
+        if (s != FMX_OK) return s;
+    }
+    return fmx_sync(g);
+}
+
+fmx_status fmx_diagnostics(fmx_grid *g, fmx_diag *out) {
+    if (!g || !out) return fail(FMX_EINVAL, "NULL argument");
+    if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
+    double co[FMX_NCOEF];
+    memcpy(co, g->co, sizeof(co));
+    const fmx::Coef<double> c = make_coef<double>(co);
+    int nl;
+    if (g->p.precision == FMX_F64) {
+        double *E[3], *B[3];
+        for (int q = 0; q < 3; ++q) { E[q] = (double *)g->buf.E[g->cur][q]; B[q] = (double *)g->buf.B[g->cur][q]; }
+        nl = fmx::launch_diagnostics<double>(g->geo, g->p.dims, c, g->p.d, E, B, g->partials,
+                                             fmx::staged_partial_slots(g->geo) * 8, g->diag_out, g->stream);
+    } else {
+        float *E[3], *B[3];
+        for (int q = 0; q < 3; ++q) { E[q] = (float *)g->buf.E[g->cur][q]; B[q] = (float *)g->buf.B[g->cur][q]; }
+        nl = fmx::launch_diagnostics<float>(g->geo, g->p.dims, c, g->p.d, E, B, g->partials,
+                                            fmx::staged_partial_slots(g->geo) * 8, g->diag_out, g->stream);
+    }
+    if (nl < 0) return fail(FMX_EINVAL, "diagnostics partial buffer too small");
+    g->launches += nl;
+    fmx_status s = check_launch(g, "diagnostics launch");
+    if (s != FMX_OK) return s;
+    double h[6];
+    cudaError_t e = cudaMemcpyAsync(h, g->diag_out, sizeof(h), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "diagnostics read-back");
+    double dv = 1.0;
+    for (int a = 0; a < g->p.dims; ++a) dv *= g->p.d[a];
+    out->w_scheme = h[0] * dv / (8.0 * M_PI);
+    out->w_plain = h[1] * dv / (8.0 * M_PI);
+    out->divb_max = h[2];
+    out->divb_l2 = sqrt(h[3]);
+    out->gauss_max = h[4];
+    out->gauss_l2 = sqrt(h[5]);
+    out->last_resid = g->last_resid;
+    out->last_sweeps = g->last_sweeps;
+    out->total_sweeps = g->total_sweeps;
+    out->steps = g->steps;
+    return FMX_OK;
+}
+
+fmx_status fmx_sync(fmx_grid *g) {
+    if (!g) return fail(FMX_EINVAL, "NULL grid");
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "pending CUDA error");
+    if (g->bound && g->st) {
+        fmx::DevStatus hs;
+        e = cudaMemcpy(&hs, g->st, sizeof(hs), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "status read-back");
+        if (hs.err) return fail((fmx_status)hs.err, "device reported status %d", hs.err);
+    }
+    return FMX_OK;
+}
+
+fmx_status fmx_coefficients(const fmx_grid *g, double *out, int n) {
+    if (!g || !out) return fail(FMX_EINVAL, "NULL argument");
+    if (n < FMX_NCOEF) return fail(FMX_EINVAL, "need room for %d coefficients", FMX_NCOEF);
+    memcpy(out, g->co, sizeof(g->co));
+    return FMX_OK;
+}
+
+double fmx_time_step(const fmx_grid *g) { return g ? g->dt : 0.0; }
+
+void *fmx_field_ptr(const fmx_grid *g, int c) {
+    if (!g || !g->bound || c < 0 || c > 8) return nullptr;
+    if (c < 3) return g->buf.E[g->cur][c];
+    if (c < 6) return g->buf.B[g->cur][c - 3];
+    return g->buf.J[c - 6];
+}
+
+int64_t fmx_launch_count(const fmx_grid *g) { return g ? g->launches : 0; }
+
+void fmx_destroy(fmx_grid *g) { delete g; }
+
+const char *fmx_strerror(fmx_status s) {
+    switch (s) {
+        case FMX_OK: return "ok";
+        case FMX_EINVAL: return "invalid argument";
+        case FMX_ECFL: return "time step above the CFL limit";
+        case FMX_ENOCONV: return "iteration did not converge within m_max sweeps";
+        case FMX_ECUDA: return "CUDA runtime error";
+        case FMX_ETIMEOUT: return "bounded device wait expired";
+        case FMX_ESTATE: return "call out of order";
+        case FMX_EUNSUPPORTED: return "unsupported combination";
+    }
+    return "unknown status";
+}
+
+const char *fmx_last_error(void) { return g_last_error; }
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// Internal declarations shared by the host API (fmx_api.cpp) and the CUDA
+// kernels of the field advance.  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fmx.h"
+
+namespace fmx {
+
+// Scalar factors of the step in the kernels' arithmetic type; same order and
+// meaning as fmx_coefficients() (Eqs. ampere_aux_x..z, matrixA_1st..last).
+template <typename T>
+struct Coef {
+    T kx, ky, kz;      // c dt / d_i
+    T q;               // 4 pi dt
+    T c6;              // 1/6: alpha = 1 + c6 Dbar^2
+    T ax, ay, az;      // (sigma_i - 1)/6, coefficient of Dbar_ii
+    T ayz, azx, axy;   // (sigma_i + sigma_j - 1)/36, coefficient of Dbar_iijj
+    T byz, bzx, bxy;   // -sigma_ij/6, coefficient of Dbar_ij (1 + Dbar_kk/6)
+};
+
+struct Geo {
+    int nx, ny, nz;
+    int64_t pitch;   // elements per row
+    int64_t plane;   // elements per z-plane = pitch * ny
+};
+
+// Device-side solver status; lives in the workspace.
+struct DevStatus {
+    double nrm2;     // ||dE'||^2 of the current solve
+    double r2;       // last ||dE_(s+1) - dE_(s)||^2
+    int count;       // sweeps done in the current solve
+    int done;        // 1 when the current solve stopped
+    int noconv;      // 1 when it stopped at m_max
+    int err;         // latched device error (FMX_ETIMEOUT, ...)
+};
+
+// Pointers of one staged step (all device).
+template <typename T>
+struct StagedPtrs {
+    T *E[3];
+    T *B[3];
+    const T *J[3];    // raw current or nullptr
+    T *jf[3];         // filtered current (workspace)
+    T *tmp;           // one scratch component (workspace)
+    T *dEp[3];        // dE' (workspace)
+    T *dEa[3];        // sweep ping (workspace)
+    T *dEb[3];        // sweep pong (workspace)
+    double *partials; // FP64 block partial sums (workspace)
+    DevStatus *st;    // status block (workspace)
+};
+
+// Number of FP64 partial slots the staged kernels need for a grid.
+int64_t staged_partial_slots(const Geo &g);
+
+// Launchers (staged.cu).  Each returns the number of kernels it enqueued.
+template <typename T>
+int launch_filter_pass(const Geo &g, int dims, const T *in, T *out, int axis, cudaStream_t s);
+
+template <typename T>
+int launch_staged_source(const Geo &g, int dims, const Coef<T> &c, const StagedPtrs<T> &p,
+                         const T *const jsrc[3], cudaStream_t s, bool norm);
+
+template <typename T>
+int launch_staged_sweep(const Geo &g, int dims, const Coef<T> &c, const StagedPtrs<T> &p, const T *const in[3],
+                        T *const out[3], bool resid, cudaStream_t s);
+
+template <typename T>
+int launch_resid_sweep(const Geo &g, int dims, const Coef<T> &c, const StagedPtrs<T> &p, cudaStream_t s);
+
+int launch_resid_init(double *partials, int64_t nparts, DevStatus *st, cudaStream_t s);
+int launch_resid_update(double *partials, int64_t nparts, DevStatus *st, double tol2, int m_max, cudaStream_t s);
+
+template <typename T>
+int launch_update_e(const Geo &g, T *const E[3], const T *const dE[3], cudaStream_t s);
+
+template <typename T>
+int launch_update_e_resid(const Geo &g, const StagedPtrs<T> &p, cudaStream_t s);
+
+template <typename T>
+int launch_faraday(const Geo &g, int dims, const Coef<T> &c, T *const E[3], T *const B[3], cudaStream_t s);
+
+// Diagnostics (diag.cu): writes 6 FP64 values to out_dev (w_scheme sum,
+// w_plain sum, divb max, divb sum sq, gauss max, gauss sum sq).
+template <typename T>
+int launch_diagnostics(const Geo &g, int dims, const Coef<double> &c, const double d[3], T *const E[3],
+                       T *const B[3], double *partials, int64_t nparts, double *out_dev, cudaStream_t s);
+
+}  // namespace fmx

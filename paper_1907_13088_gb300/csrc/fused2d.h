@@ -1,0 +1,40 @@
+// Fused 2D step: one kernel launch advances (E^n, B^{n+1/2}) to
+// (E^{n+1}, B^{n+3/2}) for the whole grid with the current filter, the
+// source, m sweeps of Algorithm 1, the E update and the Faraday update kept
+// on chip.  Internal; see fused2d.cu.
+#pragma once
+
+#include "fmx_internal.h"
+
+namespace fmx {
+
+template <typename T>
+struct Fused2dArgs {
+    const T *E[3];   // E^n
+    const T *B[3];   // B^{n+1/2}
+    const T *J[3];   // j^{n+1/2} or nullptr (vacuum)
+    T *Eo[3];        // E^{n+1} (must not alias E)
+    T *Bo[3];        // B^{n+3/2} (must not alias B)
+    int m;           // sweeps of Algorithm 1
+    int passes;      // binomial passes on the current (0 when J is nullptr)
+};
+
+// True when the fused kernel covers the problem (2D, fixed sweeps, current
+// or no filter, instantiated sweep and pass counts).
+bool fused2d_supported(const fmx_params *p);
+
+// Enqueues one step; returns the number of kernels launched (1) or -1 when
+// the (m, passes) pair is not instantiated.
+template <typename T>
+int launch_fused2d(const Geo &g, const Coef<T> &c, const Fused2dArgs<T> &a, cudaStream_t s);
+
+// Launch geometry the fused kernel picks for a grid (for tests and the
+// roofline bookkeeping): strip width, rows per segment, strips, segments,
+// threads per block.
+struct Fused2dShape {
+    int threads, halo, width, rows, strips, segments;
+};
+template <typename T>
+Fused2dShape fused2d_shape(const Geo &g, int m, int passes);
+
+}  // namespace fmx

@@ -1,0 +1,326 @@
+"""Python binding of the fmx C ABI (``include/fmx.h``).
+
+Argument marshalling only: every step of the field advance runs in the CUDA
+kernels of ``_build/libfmx.so``.  The functions below carry the C names and
+take plain integers, floats and pointers; ``Grid`` is a convenience wrapper
+that allocates the device buffers the library borrows with PyTorch (device
+memory and streams are the only things PyTorch provides here).
+
+Importing this module never falls back to anything: if the shared library is
+missing or fails to load, the import raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfmx.so")
+
+# status codes
+FMX_OK, FMX_EINVAL, FMX_ECFL, FMX_ENOCONV, FMX_ECUDA, FMX_ETIMEOUT, FMX_ESTATE, FMX_EUNSUPPORTED = range(8)
+FMX_F32, FMX_F64 = 0, 1
+FMX_ITER_FIXED, FMX_ITER_RESIDUAL = 0, 1
+FMX_FILTER_NONE, FMX_FILTER_CURRENT, FMX_FILTER_FIELDS = 0, 1, 2
+FMX_ENGINE_AUTO, FMX_ENGINE_STAGED, FMX_ENGINE_FUSED = 0, 1, 2
+FMX_HOST, FMX_DEVICE = 0, 1
+FMX_EX, FMX_EY, FMX_EZ, FMX_BX, FMX_BY, FMX_BZ, FMX_JX, FMX_JY, FMX_JZ = (1 << i for i in range(9))
+FMX_E, FMX_B, FMX_J = 7, 7 << 3, 7 << 6
+FMX_WARN_ANORM = 1
+FMX_NCOEF = 14
+
+
+class fmx_params(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("d", ctypes.c_double * 3),
+                ("c", ctypes.c_double), ("dt", ctypes.c_double), ("courant", ctypes.c_double),
+                ("precision", ctypes.c_int), ("iter_mode", ctypes.c_int), ("m", ctypes.c_int),
+                ("tol", ctypes.c_double), ("m_max", ctypes.c_int), ("filter_passes", ctypes.c_int),
+                ("filter_target", ctypes.c_int), ("lumped", ctypes.c_int), ("engine", ctypes.c_int),
+                ("pitch", ctypes.c_int64), ("stream", ctypes.c_void_p)]
+
+
+class fmx_buffers(ctypes.Structure):
+    _fields_ = [("E", (ctypes.c_void_p * 3) * 2), ("B", (ctypes.c_void_p * 3) * 2), ("J", ctypes.c_void_p * 3),
+                ("work", ctypes.c_void_p), ("work_bytes", ctypes.c_size_t)]
+
+
+class fmx_diag(ctypes.Structure):
+    _fields_ = [("w_scheme", ctypes.c_double), ("w_plain", ctypes.c_double), ("divb_max", ctypes.c_double),
+                ("divb_l2", ctypes.c_double), ("gauss_max", ctypes.c_double), ("gauss_l2", ctypes.c_double),
+                ("last_resid", ctypes.c_double), ("last_sweeps", ctypes.c_int), ("total_sweeps", ctypes.c_int64),
+                ("steps", ctypes.c_int64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"fmx CUDA library not built ({LIB_PATH}); run paper_1907_13088_gb300.build")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER(fmx_params)
+    G = ctypes.c_void_p
+    vpp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "fmx_create": (ctypes.c_int, [P, ctypes.POINTER(G), ctypes.POINTER(ctypes.c_int)]),
+        "fmx_field_bytes": (ctypes.c_size_t, [P]),
+        "fmx_workspace_bytes": (ctypes.c_size_t, [P]),
+        "fmx_bind": (ctypes.c_int, [G, ctypes.POINTER(fmx_buffers)]),
+        "fmx_set_fields": (ctypes.c_int, [G, ctypes.c_uint, vpp, ctypes.c_int]),
+        "fmx_set_current": (ctypes.c_int, [G, vpp, ctypes.c_int]),
+        "fmx_step": (ctypes.c_int, [G, ctypes.c_int]),
+        "fmx_filter": (ctypes.c_int, [G, ctypes.c_uint, ctypes.c_int]),
+        "fmx_get_fields": (ctypes.c_int, [G, ctypes.c_uint, vpp, ctypes.c_int]),
+        "fmx_diagnostics": (ctypes.c_int, [G, ctypes.POINTER(fmx_diag)]),
+        "fmx_sync": (ctypes.c_int, [G]),
+        "fmx_coefficients": (ctypes.c_int, [G, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+        "fmx_time_step": (ctypes.c_double, [G]),
+        "fmx_field_ptr": (ctypes.c_void_p, [G, ctypes.c_int]),
+        "fmx_launch_count": (ctypes.c_int64, [G]),
+        "fmx_destroy": (None, [G]),
+        "fmx_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "fmx_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib, sig
+
+
+_lib, ABI_SIGNATURES = _load()
+
+fmx_create = _lib.fmx_create
+fmx_field_bytes = _lib.fmx_field_bytes
+fmx_workspace_bytes = _lib.fmx_workspace_bytes
+fmx_bind = _lib.fmx_bind
+fmx_set_fields = _lib.fmx_set_fields
+fmx_set_current = _lib.fmx_set_current
+fmx_step = _lib.fmx_step
+fmx_filter = _lib.fmx_filter
+fmx_get_fields = _lib.fmx_get_fields
+fmx_diagnostics = _lib.fmx_diagnostics
+fmx_sync = _lib.fmx_sync
+fmx_coefficients = _lib.fmx_coefficients
+fmx_time_step = _lib.fmx_time_step
+fmx_field_ptr = _lib.fmx_field_ptr
+fmx_launch_count = _lib.fmx_launch_count
+fmx_destroy = _lib.fmx_destroy
+fmx_strerror = _lib.fmx_strerror
+fmx_last_error = _lib.fmx_last_error
+
+
+class FmxError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = fmx_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {fmx_strerror(status).decode()} ({status}): {msg}")
+
+
+def check(status: int, where: str = "fmx") -> None:
+    if status != FMX_OK:
+        raise FmxError(status, where)
+
+
+def make_params(shape, d=(1.0, 1.0, 1.0), c=1.0, dt=0.0, courant=0.5, precision=FMX_F32, iter_mode=FMX_ITER_FIXED,
+                m=4, tol=1e-13, m_max=10000, filter_passes=0, filter_target=FMX_FILTER_CURRENT, lumped=False,
+                engine=FMX_ENGINE_AUTO, pitch=0, stream=None) -> fmx_params:
+    """fmx_params for a grid of ``shape`` = (nx,), (nx, ny) or (nx, ny, nz)."""
+    p = fmx_params()
+    p.dims = len(shape)
+    n3 = tuple(shape) + (1,) * (3 - len(shape))
+    for a in range(3):
+        p.n[a] = int(n3[a])
+        p.d[a] = float(d[a]) if a < len(d) else 1.0
+    p.c, p.dt, p.courant = float(c), float(dt or 0.0), float(courant)
+    p.precision, p.iter_mode, p.m = int(precision), int(iter_mode), int(m)
+    p.tol, p.m_max = float(tol), int(m_max)
+    p.filter_passes, p.filter_target, p.lumped = int(filter_passes), int(filter_target), int(bool(lumped))
+    p.engine, p.pitch = int(engine), int(pitch)
+    p.stream = stream
+    return p
+
+
+class Grid:
+    """A field-advance grid whose device buffers are PyTorch tensors.
+
+    Fields are exchanged as arrays of shape (3, nz, ny, nx) (numpy on the
+    host or torch tensors on the device) at the staggered positions
+    documented in fmx.h.
+    """
+
+    def __init__(self, shape, device="cuda", with_current=True, **kw):
+        import torch
+
+        self.torch = torch
+        self.shape = tuple(shape)
+        self.device = torch.device(device)
+        stream = kw.pop("stream", None)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        kw.setdefault("precision", FMX_F32)
+        self.params = make_params(shape, stream=ctypes.c_void_p(stream.cuda_stream), **kw)
+        self.dtype = torch.float64 if self.params.precision == FMX_F64 else torch.float32
+        self.np_dtype = np.float64 if self.params.precision == FMX_F64 else np.float32
+        h = ctypes.c_void_p()
+        warn = ctypes.c_int(0)
+        check(fmx_create(ctypes.byref(self.params), ctypes.byref(h), ctypes.byref(warn)), "fmx_create")
+        self.handle = h
+        self.warnings = warn.value
+        fb = fmx_field_bytes(ctypes.byref(self.params))
+        wb = fmx_workspace_bytes(ctypes.byref(self.params))
+        esz = 8 if self.params.precision == FMX_F64 else 4
+        nfield = (fb + 255) // 256 * 256 // esz
+        ncomp = 12 + (3 if with_current else 0)
+        # one slab for every field component, each at a 256-byte boundary
+        self._slab = torch.zeros(ncomp * nfield, dtype=self.dtype, device=self.device)
+        self._work = torch.zeros((wb + 511) // 256 * 256, dtype=torch.uint8, device=self.device)
+        base = self._slab.data_ptr()
+        wbase = (self._work.data_ptr() + 255) // 256 * 256
+        ptr = lambda i: base + i * nfield * esz
+        b = fmx_buffers()
+        for s in range(2):
+            for c in range(3):
+                b.E[s][c] = ptr(s * 6 + c)
+                b.B[s][c] = ptr(s * 6 + 3 + c)
+        for c in range(3):
+            b.J[c] = ptr(12 + c) if with_current else None
+        b.work = wbase
+        b.work_bytes = wb
+        self.buffers = b
+        check(fmx_bind(self.handle, ctypes.byref(b)), "fmx_bind")
+        nx, ny, nz = self.shape + (1,) * (3 - len(self.shape))
+        self.array_shape = (3, nz, ny, nx)
+
+    # -- lifetime --------------------------------------------------------
+    def close(self):
+        if getattr(self, "handle", None):
+            fmx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- copies ----------------------------------------------------------
+    def _ptr_array(self, arrays):
+        keep = []
+        ptrs = (ctypes.c_void_p * len(arrays))()
+        for i, a in enumerate(arrays):
+            if a is None:
+                ptrs[i] = None
+            elif isinstance(a, np.ndarray):
+                a = np.ascontiguousarray(a, dtype=self.np_dtype)
+                keep.append(a)
+                ptrs[i] = a.ctypes.data
+            else:
+                a = a.contiguous()
+                keep.append(a)
+                ptrs[i] = a.data_ptr()
+        return ptrs, keep
+
+    def set_fields(self, E=None, B=None):
+        arrs = [None] * 6
+        mask = 0
+        where = FMX_HOST
+        for k, F in enumerate((E, B)):
+            if F is None:
+                continue
+            for c in range(3):
+                arrs[3 * k + c] = F[c]
+                mask |= 1 << (3 * k + c)
+            where = FMX_HOST if isinstance(F, np.ndarray) else FMX_DEVICE
+        ptrs, keep = self._ptr_array(arrs)
+        check(fmx_set_fields(self.handle, mask, ptrs, where), "fmx_set_fields")
+        del keep
+
+    def set_current(self, J):
+        ptrs, keep = self._ptr_array([J[0], J[1], J[2]])
+        where = FMX_HOST if isinstance(J, np.ndarray) else FMX_DEVICE
+        check(fmx_set_current(self.handle, ptrs, where), "fmx_set_current")
+        del keep
+
+    def get_fields(self, mask=FMX_E | FMX_B, out=None, host_out=None):
+        """Copies the components in mask to host numpy arrays (``host_out``
+        when given, e.g. pinned memory, shape (9, nz, ny, nx)) or into the
+        given device tensors ``out`` of that shape.  Returns E, B, J arrays of
+        shape (3, nz, ny, nx) (None where not requested)."""
+        nz, ny, nx = self.array_shape[1:]
+        if out is None:
+            host = host_out if host_out is not None else np.zeros((9, nz, ny, nx), dtype=self.np_dtype)
+            ptrs = (ctypes.c_void_p * 9)(*[host[c].ctypes.data if mask & (1 << c) else None for c in range(9)])
+            check(fmx_get_fields(self.handle, mask, ptrs, FMX_HOST), "fmx_get_fields")
+            res = host
+        else:
+            ptrs = (ctypes.c_void_p * 9)(*[out[c].data_ptr() if mask & (1 << c) else None for c in range(9)])
+            check(fmx_get_fields(self.handle, mask, ptrs, FMX_DEVICE), "fmx_get_fields")
+            res = out
+        E = res[0:3] if mask & FMX_E else None
+        B = res[3:6] if mask & FMX_B else None
+        J = res[6:9] if mask & FMX_J else None
+        return E, B, J
+
+    # -- work ------------------------------------------------------------
+    def step(self, nsteps=1):
+        check(fmx_step(self.handle, int(nsteps)), "fmx_step")
+
+    def filter(self, mask, passes):
+        check(fmx_filter(self.handle, int(mask), int(passes)), "fmx_filter")
+
+    def sync(self):
+        check(fmx_sync(self.handle), "fmx_sync")
+
+    def diagnostics(self) -> dict:
+        d = fmx_diag()
+        check(fmx_diagnostics(self.handle, ctypes.byref(d)), "fmx_diagnostics")
+        return {k: getattr(d, k) for k, _ in fmx_diag._fields_}
+
+    def coefficients(self) -> np.ndarray:
+        out = (ctypes.c_double * FMX_NCOEF)()
+        check(fmx_coefficients(self.handle, out, FMX_NCOEF), "fmx_coefficients")
+        return np.array(out[:])
+
+    @property
+    def dt(self) -> float:
+        return fmx_time_step(self.handle)
+
+    @property
+    def launches(self) -> int:
+        return int(fmx_launch_count(self.handle))
+
+    def field_tensor(self, c: int):
+        """Zero-copy torch view of component c (0..5 E/B current state, 6..8 J),
+        shape (nz, ny, pitch)."""
+        ptr = fmx_field_ptr(self.handle, c)
+        if not ptr:
+            return None
+        base = self._slab.data_ptr()
+        esz = self._slab.element_size()
+        off = (ptr - base) // esz
+        nx, ny, nz = self.shape + (1,) * (3 - len(self.shape))
+        pitch = self.params.pitch or (nx + (16 // esz) - 1) // (16 // esz) * (16 // esz)
+        return self._slab[off:off + pitch * ny * nz].view(nz, ny, pitch)
+
+
+def coefficients_of(params: fmx_params) -> np.ndarray:
+    """Coefficients of a parameter set (host only; creates and frees a handle)."""
+    h = ctypes.c_void_p()
+    check(fmx_create(ctypes.byref(params), ctypes.byref(h), None), "fmx_create")
+    try:
+        out = (ctypes.c_double * FMX_NCOEF)()
+        check(fmx_coefficients(h, out, FMX_NCOEF), "fmx_coefficients")
+        return np.array(out[:])
+    finally:
+        fmx_destroy(h)
+
+
+def create_status(params: fmx_params):
+    """Returns (status, warnings) of fmx_create for a parameter set (host only)."""
+    h = ctypes.c_void_p()
+    w = ctypes.c_int(0)
+    s = fmx_create(ctypes.byref(params), ctypes.byref(h), ctypes.byref(w))
+    if s == FMX_OK:
+        fmx_destroy(h)
+    return s, w.value

@@ -1,0 +1,110 @@
+"""Host-side checks of the C ABI: the library loads, exports every entry
+point of include/fmx.h, validates its parameters, and uses exactly the
+coefficients the oracle derives independently (no GPU needed)."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import core
+from paper_1907_13088_gb300 import build as fbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fmx():
+    fbuild.build()
+    from paper_1907_13088_gb300 import fmx as m
+    return m
+
+
+def _declared():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names += re.findall(r"\b(fmx_[a-z0-9_]+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(fmx):
+    import ctypes
+    lib = ctypes.CDLL(fmx.LIB_PATH)
+    declared = _declared()
+    assert len(declared) >= 18
+    for name in declared:
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+    assert set(declared) <= set(fmx.ABI_SIGNATURES)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("case", [
+    dict(shape=(64, 64), courant=0.5), dict(shape=(4096, 4096), courant=0.5),
+    dict(shape=(33, 17, 9), d=(1.0, 0.7, 1.3), courant=0.61), dict(shape=(100,), courant=0.9),
+    dict(shape=(20, 30), d=(0.5, 2.0, 1.0), courant=1.0), dict(shape=(8, 8), courant=0.3, lumped=True)])
+def test_coefficients_bitwise_equal_oracle(fmx, prec, case):
+    case = dict(case)
+    lumped = case.pop("lumped", False)
+    p = fmx.make_params(case["shape"], d=case.get("d", (1.0, 1.0, 1.0)), courant=case["courant"],
+                        precision=prec, lumped=lumped, engine=fmx.FMX_ENGINE_STAGED)
+    got = fmx.coefficients_of(p)
+    o = core.Params(shape=case["shape"], d=case.get("d", (1.0, 1.0, 1.0)), courant=case["courant"],
+                    lumped=lumped, coef_f32=(prec == 0))
+    want = np.array([core.coefficients(o)[n] for n in core.COEF_NAMES])
+    assert np.array_equal(got, want), (got, want)
+    # and the time step is the oracle's dt = courant * dt_CFL
+    h = __import__("ctypes").c_void_p()
+    fmx.check(fmx.fmx_create(__import__("ctypes").byref(p), __import__("ctypes").byref(h), None))
+    assert fmx.fmx_time_step(h) == o.time_step()
+    fmx.fmx_destroy(h)
+
+
+def test_validation_codes(fmx):
+    ok = fmx.make_params((16, 16), courant=0.5)
+    assert fmx.create_status(ok) == (fmx.FMX_OK, 0)
+    # Eq. dt_cfl_3d: above the limit -> FMX_ECFL
+    bad = fmx.make_params((16, 16), dt=1.0 / math.sqrt(2) * 1.001)
+    assert fmx.create_status(bad)[0] == fmx.FMX_ECFL
+    assert fmx.create_status(fmx.make_params((16, 16), dt=1.0 / math.sqrt(2)))[0] == fmx.FMX_OK
+    assert fmx.create_status(fmx.make_params((16, 16), courant=1.2))[0] == fmx.FMX_ECFL
+    # 3D non-cubic with dt > min(d)/(sqrt(2) c): App. C bound not guaranteed -> warning
+    s, w = fmx.create_status(fmx.make_params((8, 8, 8), d=(1.0, 1.0, 0.3), courant=0.99))
+    assert s == fmx.FMX_OK and w & fmx.FMX_WARN_ANORM
+    s, w = fmx.create_status(fmx.make_params((8, 8, 8), courant=0.99))
+    assert s == fmx.FMX_OK and w == 0
+    p = fmx.make_params((16, 16))
+    p.dims = 4
+    assert fmx.create_status(p)[0] == fmx.FMX_EINVAL
+    p = fmx.make_params((16, 16))
+    p.n[2] = 3
+    assert fmx.create_status(p)[0] == fmx.FMX_EINVAL
+    assert fmx.create_status(fmx.make_params((16, 16), pitch=17))[0] == fmx.FMX_EINVAL
+    assert fmx.create_status(fmx.make_params((16, 16), iter_mode=1, tol=0.0))[0] == fmx.FMX_EINVAL
+    assert fmx.create_status(fmx.make_params((16, 16), m=-1))[0] == fmx.FMX_EINVAL
+    # the fused engine covers 2D fixed sweeps only
+    assert fmx.create_status(fmx.make_params((16, 16, 16), engine=fmx.FMX_ENGINE_FUSED))[0] == fmx.FMX_EUNSUPPORTED
+    assert fmx.create_status(fmx.make_params((16, 16), iter_mode=1, engine=fmx.FMX_ENGINE_FUSED))[0] == \
+        fmx.FMX_EUNSUPPORTED
+    assert fmx.create_status(fmx.make_params((16, 16), engine=fmx.FMX_ENGINE_FUSED, m=4, filter_passes=3))[0] == \
+        fmx.FMX_OK
+    assert b"CFL" in fmx.fmx_strerror(fmx.FMX_ECFL)
+
+
+def test_sizes(fmx):
+    import ctypes
+    p = fmx.make_params((4099, 31), precision=0)
+    assert fmx.fmx_field_bytes(ctypes.byref(p)) == 4100 * 31 * 4
+    p = fmx.make_params((4099, 31), precision=1)
+    assert fmx.fmx_field_bytes(ctypes.byref(p)) == 4100 * 31 * 8
+    p = fmx.make_params((10, 6, 5), precision=0, pitch=16)
+    assert fmx.fmx_field_bytes(ctypes.byref(p)) == 16 * 6 * 5 * 4
+    staged = fmx.make_params((1000, 1000), engine=fmx.FMX_ENGINE_STAGED)
+    fused = fmx.make_params((1000, 1000), engine=fmx.FMX_ENGINE_FUSED)
+    fb = fmx.fmx_field_bytes(ctypes.byref(staged))
+    assert fmx.fmx_workspace_bytes(ctypes.byref(staged)) >= 13 * fb
+    assert fmx.fmx_workspace_bytes(ctypes.byref(fused)) < 2 * fb
+    bad = fmx.make_params((16, 16), courant=2.0)
+    assert fmx.fmx_workspace_bytes(ctypes.byref(bad)) == 0

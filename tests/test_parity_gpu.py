@@ -1,0 +1,284 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances, per field component, relative L2 ||gpu - oracle|| / ||oracle||:
+FP64 path 1e-12, FP32 path 1e-5.  FP32 runs start from the FP32-rounded
+inputs and the oracle uses the FP32-rounded coefficients the kernels
+multiply by (the oracle still computes in FP64).
+"""
+import numpy as np
+import pytest
+
+from oracle import core
+from paper_1907_13088_gb300 import synth
+from tests.helpers import assert_parity, periodic_window, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL64, TOL32 = 1e-12, 1e-5
+
+
+@pytest.fixture(scope="module")
+def fmx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_13088_gb300 import build
+    build.build()
+    from paper_1907_13088_gb300 import fmx as m
+    return m
+
+
+def _run_gpu(fmx, shape, E, B, J, nsteps, **kw):
+    g = fmx.Grid(shape, with_current=J is not None, **kw)
+    g.set_fields(E, B)
+    if J is not None:
+        g.set_current(J)
+    g.step(nsteps)
+    E1, B1, _ = g.get_fields()
+    info = {"launches": g.launches, "diag": None, "grid": g}
+    return np.array(E1, dtype=np.float64), np.array(B1, dtype=np.float64), info
+
+
+def _oracle(shape, E, B, J, nsteps, **kw):
+    p = core.Params(shape=tuple(shape), **kw)
+    E1, B1, rc, st = core.step(p, E, B, J, nsteps)
+    return E1, B1, rc, st
+
+
+def _inputs(shape, seed, dtype, with_j=True, smooth=False):
+    if smooth:
+        kmax = max(2, min(shape) // 8)
+        E, B = synth.power_law_fields(shape, kmax, seed, dtype=np.float64)
+        J = synth.solenoidal_current(shape, seed + 1, width=2.0, rms=1e-2, dtype=np.float64) if with_j else None
+    else:
+        E, B, J = synth.random_fields(shape, seed)
+        if not with_j:
+            J = None
+    E = E.astype(dtype)
+    B = B.astype(dtype)
+    J = J.astype(dtype) if J is not None else None
+    return E, B, J
+
+
+ENGINE = {"staged": 1, "fused": 2}
+
+
+# ---------------------------------------------------------------------------
+# FP64, both engines, 1D/2D/3D, ragged sizes, every filter/sweep count
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(37, 29), (5, 3), (1, 8), (7, 1), (300, 41)])
+@pytest.mark.parametrize("engine", ["staged", "fused"])
+def test_fp64_2d_random(fmx, shape, engine):
+    E, B, J = _inputs(shape, 21, np.float64)
+    Eg, Bg, _ = _run_gpu(fmx, shape, E, B, J, 6, precision=1, m=4, filter_passes=3, engine=ENGINE[engine])
+    Eo, Bo, rc, _ = _oracle(shape, E, B, J, 6, m=4, filter_passes=3)
+    assert_parity(Eg, Bg, Eo, Bo, TOL64, f"{engine} {shape}")
+
+
+@pytest.mark.parametrize("m", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("passes", [0, 1, 2, 3, None])
+def test_fused_fp64_every_instantiation(fmx, m, passes):
+    shape = (53, 47)
+    E, B, J = _inputs(shape, 100 + m, np.float64, with_j=passes is not None)
+    p = passes or 0
+    Eg, Bg, _ = _run_gpu(fmx, shape, E, B, J, 5, precision=1, m=m, filter_passes=p, engine=2, courant=0.8)
+    Eo, Bo, rc, _ = _oracle(shape, E, B, J, 5, m=m, filter_passes=p, courant=0.8)
+    assert_parity(Eg, Bg, Eo, Bo, TOL64, f"fused m={m} p={passes}")
+
+
+@pytest.mark.parametrize("shape", [(13, 11, 7), (9, 8, 6), (40,), (17, 1, 5)])
+def test_staged_fp64_3d_1d(fmx, shape):
+    E, B, J = _inputs(shape, 31, np.float64)
+    kw = dict(m=3, filter_passes=1, courant=0.7, d=(1.0, 0.8, 1.2))
+    Eg, Bg, _ = _run_gpu(fmx, shape, E, B, J, 5, precision=1, engine=1, **kw)
+    Eo, Bo, rc, _ = _oracle(shape, E, B, J, 5, **kw)
+    assert_parity(Eg, Bg, Eo, Bo, TOL64, f"staged {shape}")
+
+
+def test_staged_fields_filter_and_lumped(fmx):
+    shape = (24, 18)
+    E, B, J = _inputs(shape, 41, np.float64)
+    kw = dict(m=2, filter_passes=2, filter_target=core.FILTER_FIELDS, courant=0.6)
+    Eg, Bg, _ = _run_gpu(fmx, shape, E, B, J, 4, precision=1, engine=1, **kw)
+    Eo, Bo, rc, _ = _oracle(shape, E, B, J, 4, **kw)
+    assert_parity(Eg, Bg, Eo, Bo, TOL64, "fields filter")
+    for eng in (1, 2):
+        Eg, Bg, _ = _run_gpu(fmx, shape, E, B, J, 4, precision=1, engine=eng, lumped=True, filter_passes=1)
+        Eo, Bo, rc, _ = _oracle(shape, E, B, J, 4, lumped=True, filter_passes=1)
+        assert_parity(Eg, Bg, Eo, Bo, TOL64, f"lumped engine {eng}")
+
+
+# ---------------------------------------------------------------------------
+# residual mode: the 64x64 FP64 plane-wave case (200 steps, tol 1e-13)
+# ---------------------------------------------------------------------------
+
+def test_residual_mode_plane_waves_64(fmx):
+    shape = (64, 64)
+    po = core.Params(shape=shape, courant=0.5, residual=True, tol=1e-13, m_max=10000)
+    E, B, _ = synth.tm_plane_waves(shape, po.time_step(), seed=1907001)
+    Eg, Bg, info = _run_gpu(fmx, shape, E, B, None, 200, precision=1, iter_mode=1, tol=1e-13, m_max=10000,
+                            courant=0.5)
+    d = info["grid"].diagnostics()
+    Eo, Bo, rc, st = _oracle(shape, E, B, None, 200, courant=0.5, residual=True, tol=1e-13, m_max=10000)
+    assert rc == core.OK
+    errs = assert_parity(Eg, Bg, Eo, Bo, TOL64, "residual 64x64")
+    assert d["last_sweeps"] == st["last_sweeps"] and d["total_sweeps"] == st["total_sweeps"]
+    assert d["steps"] == 200
+    # TE part stays exactly zero (Sec. 2.2.2 decoupling)
+    assert np.all(Eg[:2] == 0) and np.all(Bg[2] == 0)
+    del errs
+
+
+def test_residual_mode_noconv(fmx):
+    shape = (16, 16)
+    E, B, J = _inputs(shape, 5, np.float64)
+    g = fmx.Grid(shape, with_current=False, precision=1, iter_mode=1, tol=1e-15, m_max=3, engine=1)
+    g.set_fields(E, B)
+    with pytest.raises(fmx.FmxError) as ei:
+        g.step(1)
+    assert ei.value.status == fmx.FMX_ENOCONV
+
+
+# ---------------------------------------------------------------------------
+# FP32 against the oracle with FP32-rounded coefficients
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("engine", ["staged", "fused"])
+@pytest.mark.parametrize("shape,nsteps", [((96, 80), 100), ((517, 263), 20)])
+def test_fp32_smooth_fields(fmx, engine, shape, nsteps):
+    E, B, J = _inputs(shape, 51, np.float32, smooth=True)
+    Eg, Bg, _ = _run_gpu(fmx, shape, E, B, J, nsteps, precision=0, m=4, filter_passes=3, engine=ENGINE[engine])
+    Eo, Bo, rc, _ = _oracle(shape, E.astype(np.float64), B.astype(np.float64), J.astype(np.float64), nsteps,
+                            m=4, filter_passes=3, coef_f32=True)
+    assert_parity(Eg, Bg, Eo, Bo, TOL32, f"fp32 {engine} {shape}")
+
+
+def test_engines_agree_fp64(fmx):
+    shape = (611, 233)
+    E, B, J = _inputs(shape, 61, np.float64, smooth=True)
+    E1, B1, _ = _run_gpu(fmx, shape, E, B, J, 8, precision=1, m=4, filter_passes=3, engine=1)
+    E2, B2, _ = _run_gpu(fmx, shape, E, B, J, 8, precision=1, m=4, filter_passes=3, engine=2)
+    assert_parity(E2, B2, E1, B1, 1e-13, "fused vs staged")
+
+
+# ---------------------------------------------------------------------------
+# the benchmark configuration at full size: 4096^2 FP32, m = 4, 3 passes,
+# in the fused launch bench.py times; sampled windows against the oracle
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nsteps", [1, 3])
+def test_full_size_4096_windows(fmx, nsteps):
+    shape = (4096, 4096)
+    E, B = synth.power_law_fields(shape, 512, 1907002)
+    J = synth.solenoidal_current(shape, 1907003, width=16.0, rms=1e-3)
+    g = fmx.Grid(shape, precision=0, m=4, filter_passes=3, engine=2, courant=0.5)
+    g.set_fields(E, B)
+    g.set_current(J)
+    g.step(nsteps)
+    Eg, Bg, _ = g.get_fields()
+    radius = 8 * nsteps  # one step reaches 8 cells (3 filter + 4 sweeps + 1 curl)
+    size = 2 * radius + 40
+    rng = np.random.default_rng(7)
+    centers = [(0, 0), (4095, 4095), (0, 2048), (2048, 4095)] + [tuple(rng.integers(0, 4096, 2)) for _ in range(6)]
+    p = core.Params(shape=(size, size), courant=0.5, m=4, filter_passes=3, coef_f32=True)
+    worst = 0.0
+    for cy, cx in centers:
+        w = lambda a: periodic_window(a, (cy, cx), size).astype(np.float64)
+        Eo, Bo, rc, _ = core.step(p, w(E), w(B), w(J), nsteps)
+        lo, hi = radius + 1, size - radius - 1
+        sl = (slice(None), slice(None), slice(lo, hi), slice(lo, hi))
+        for F_g, F_o in ((Eg, Eo), (Bg, Bo)):
+            Fw = periodic_window(F_g, (cy, cx), size).astype(np.float64)
+            for c in range(3):
+                e = rel_l2(Fw[c][sl[1:]], F_o[c][sl[1:]])
+                worst = max(worst, e)
+                assert e < TOL32, (cy, cx, c, e)
+    assert g.launches == nsteps
+
+
+# ---------------------------------------------------------------------------
+# standalone filter, diagnostics, state handling
+# ---------------------------------------------------------------------------
+
+def test_standalone_filter(fmx):
+    for shape in ((33, 21), (10, 9, 7)):
+        E, B, J = _inputs(shape, 71, np.float64)
+        g = fmx.Grid(shape, precision=1, engine=1)
+        g.set_fields(E, B)
+        g.set_current(J)
+        g.filter(fmx.FMX_E | fmx.FMX_JZ, 3)
+        Eg, Bg, Jg = g.get_fields(fmx.FMX_E | fmx.FMX_B | fmx.FMX_J)
+        p = core.Params(shape=shape)
+        assert rel_l2(Eg, core.filter(p, E, 3)) < 1e-14
+        assert np.array_equal(np.asarray(Bg), B)
+        assert rel_l2(Jg[2], core.filter(p, J[2:3], 3)[0]) < 1e-14
+        assert np.array_equal(np.asarray(Jg[:2]), J[:2])
+
+
+@pytest.mark.parametrize("shape,prec", [((48, 40), 1), ((12, 10, 9), 1), ((64, 56), 0)])
+def test_diagnostics_match_oracle(fmx, shape, prec):
+    dtype = np.float64 if prec == 1 else np.float32
+    E, B, J = _inputs(shape, 81, dtype)
+    kw = dict(courant=0.7, m=3)
+    g = fmx.Grid(shape, precision=prec, engine=1, **kw)
+    g.set_fields(E, B)
+    d = g.diagnostics()
+    p = core.Params(shape=shape, coef_f32=(prec == 0), **kw)
+    E64, B64 = E.astype(np.float64), B.astype(np.float64)
+    ws, wp = core.energy(p, E64, B64)
+    db = core.div_b(p, B64)
+    ge = core.gauss_e(p, E64)
+    assert abs(d["w_scheme"] - ws) <= 1e-12 * abs(ws)
+    assert abs(d["w_plain"] - wp) <= 1e-12 * abs(wp)
+    assert abs(d["divb_max"] - np.max(np.abs(db))) <= 1e-12 * np.max(np.abs(db))
+    assert abs(d["divb_l2"] - np.linalg.norm(db)) <= 1e-12 * np.linalg.norm(db)
+    assert abs(d["gauss_max"] - np.max(np.abs(ge))) <= 1e-12 * np.max(np.abs(ge))
+    assert abs(d["gauss_l2"] - np.linalg.norm(ge)) <= 1e-12 * np.linalg.norm(ge)
+
+
+def test_zero_steps_and_state_sets(fmx):
+    shape = (40, 30)
+    E, B, J = _inputs(shape, 91, np.float32)
+    g = fmx.Grid(shape, precision=0, m=4, filter_passes=3, engine=2)
+    g.set_fields(E, B)
+    g.set_current(J)
+    g.step(0)
+    E0, B0, _ = g.get_fields()
+    assert np.array_equal(E0, E) and np.array_equal(B0, B)
+    g.step(3)  # odd count: the state now lives in set 1
+    E3, B3, _ = g.get_fields()
+    g2 = fmx.Grid(shape, precision=0, m=4, filter_passes=3, engine=2)
+    g2.set_fields(E, B)
+    g2.set_current(J)
+    for _ in range(3):
+        g2.step(1)
+    E3b, B3b, _ = g2.get_fields()
+    assert np.array_equal(E3, E3b) and np.array_equal(B3, B3b)
+    # set_fields after steps writes the current set
+    g.set_fields(E, B)
+    g.step(1)
+    E1, B1, _ = g.get_fields()
+    g3 = fmx.Grid(shape, precision=0, m=4, filter_passes=3, engine=2)
+    g3.set_fields(E, B)
+    g3.set_current(J)
+    g3.step(1)
+    E1b, B1b, _ = g3.get_fields()
+    assert np.array_equal(E1, E1b) and np.array_equal(B1, B1b)
+
+
+def test_conservation_on_gpu_fp64(fmx):
+    """div B is preserved to round-off by the GPU step for any m (App. A)."""
+    shape = (128, 96)
+    E, B, J = _inputs(shape, 95, np.float64)
+    g = fmx.Grid(shape, precision=1, m=4, filter_passes=3, engine=2)
+    g.set_fields(E, B)
+    g.set_current(J)
+    d0 = g.diagnostics()
+    g.step(50)
+    d1 = g.diagnostics()
+    p = core.Params(shape=shape)
+    Eg, Bg, _ = g.get_fields()
+    db = core.div_b(p, Bg) - core.div_b(p, B)
+    assert np.max(np.abs(db)) < 1e-11
+    assert abs(d1["divb_l2"] - d0["divb_l2"]) < 1e-10 * d0["divb_l2"]
