@@ -217,6 +217,33 @@ void *fmx_field_ptr(const fmx_grid *g, int c);
 /* Number of device kernels this grid has launched since fmx_bind. */
 int64_t fmx_launch_count(const fmx_grid *g);
 
+/* Size of the device scratch array behind fmx_step_static (4 MiB). */
+#define FMX_STATIC_SCRATCH_BYTES (4u << 20)
+
+/* fmx_step_static -- the paper has no counterpart to this call; it exists for
+ * callers that cannot allocate device memory: a host program whose device
+ * memory is owned by its own pool or a fixed budget set up front, where an
+ * extra cudaMalloc (or a PyTorch allocation) for a workspace is not allowed
+ * once the run has started.  It advances nsteps steps exactly like fmx_step
+ * with the staged engine (any dims, precision, iteration mode and filter of
+ * p; p->engine is ignored), in place on the caller's E[3] and B[3] (device
+ * arrays in the layout above with p's pitch), reading J[3] (or J == NULL for
+ * vacuum), and allocates nothing: its intermediates live in one file-scope
+ * device array of FMX_STATIC_SCRATCH_BYTES that every GPU loading the library
+ * holds until the process exits.
+ *   Limit: the grid's staged workspace (fmx_workspace_bytes with the staged
+ *   engine, about 13 field arrays) must fit in that array -- roughly 40 000
+ *   cells in FP64 or 80 000 in FP32; larger grids return FMX_EINVAL with a
+ *   message naming both sizes.
+ *   The first call on a device resolves the array's device address (with
+ *   that device current); make that first call before any stream capture.
+ *   Every call on a device shares the same array and it keeps the last call's
+ *   contents; each call clears the part that must start at zero (the solver
+ *   status) itself.  Calls whose work overlaps on the GPU (other streams,
+ *   other host threads) race on the array: serialise them.
+ *   Errors as fmx_step (FMX_EINVAL, FMX_ECFL, FMX_ENOCONV, FMX_ECUDA). */
+fmx_status fmx_step_static(const fmx_params *p, void *const *E, void *const *B, const void *const *J, int nsteps);
+
 /* Releases the handle (host memory only; borrowed buffers are untouched). */
 void fmx_destroy(fmx_grid *g);
 

@@ -630,3 +630,57 @@ const char *fmx_strerror(fmx_status s) {
 const char *fmx_last_error(void) { return g_last_error; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Helpers for entry points that supply their own workspace (static_scratch.cu).
+// ---------------------------------------------------------------------------
+namespace fmx {
+
+void set_last_error(const char *msg) { fail(FMX_EINVAL, "%s", msg); }
+
+size_t staged_workspace_bytes(const fmx_params *p) {
+    if (!p) return 0;
+    fmx_params q = *p;
+    q.engine = FMX_ENGINE_STAGED;
+    double dt;
+    if (validate(&q, &dt, nullptr) != FMX_OK) return 0;
+    return workspace_of(&q, FMX_ENGINE_STAGED);
+}
+
+fmx_status staged_steps_on(const fmx_params *p, void *const E[3], void *const B[3], const void *const J[3],
+                           void *work, size_t work_bytes, int nsteps) {
+    if (!p || !E || !B) return fail(FMX_EINVAL, "NULL argument");
+    if (nsteps < 0) return fail(FMX_EINVAL, "nsteps < 0");
+    fmx_params q = *p;
+    q.engine = FMX_ENGINE_STAGED;
+    double dt = 0.0;
+    fmx_status s = validate(&q, &dt, nullptr);
+    if (s != FMX_OK) return s;
+    fmx_grid g;  // on the stack: this path performs no allocation of any kind
+    g.p = q;
+    g.dt = dt;
+    coefficients(&q, dt, g.co);
+    g.engine = FMX_ENGINE_STAGED;
+    g.geo = geo_of(&q);
+    g.elem = elem_size(q.precision);
+    g.field_bytes = (size_t)g.geo.plane * (size_t)g.geo.nz * g.elem;
+    g.stream = (cudaStream_t)q.stream;
+    fmx_buffers b;
+    memset(&b, 0, sizeof(b));
+    for (int c = 0; c < 3; ++c) {
+        b.E[0][c] = E[c];
+        b.B[0][c] = B[c];
+        b.J[c] = J ? const_cast<void *>(J[c]) : nullptr;
+    }
+    b.work = work;
+    b.work_bytes = work_bytes;
+    s = fmx_bind(&g, &b);
+    if (s != FMX_OK) return s;
+    for (int n = 0; n < nsteps; ++n) {
+        s = q.precision == FMX_F64 ? staged_step<double>(&g) : staged_step<float>(&g);
+        if (s != FMX_OK) return s;
+    }
+    return FMX_OK;
+}
+
+}  // namespace fmx

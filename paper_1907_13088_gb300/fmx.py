@@ -79,6 +79,7 @@ def _load():
         "fmx_destroy": (None, [G]),
         "fmx_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "fmx_last_error": (ctypes.c_char_p, []),
+        "fmx_step_static": (ctypes.c_int, [P, vpp, vpp, vpp, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -107,6 +108,8 @@ fmx_launch_count = _lib.fmx_launch_count
 fmx_destroy = _lib.fmx_destroy
 fmx_strerror = _lib.fmx_strerror
 fmx_last_error = _lib.fmx_last_error
+fmx_step_static = _lib.fmx_step_static
+FMX_STATIC_SCRATCH_BYTES = 4 << 20
 
 
 class FmxError(RuntimeError):
