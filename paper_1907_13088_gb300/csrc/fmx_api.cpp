@@ -343,7 +343,13 @@ fmx_status fused_step(fmx_grid *g, int nsteps) {
         }
         a.m = g->p.m;
         a.passes = (g->p.filter_target == FMX_FILTER_CURRENT && g->buf.J[0]) ? g->p.filter_passes : 0;
-        int nl = fmx::launch_fused2d<T>(g->geo, c, a, g->stream);
+        int nl;
+        if constexpr (sizeof(T) == 4) {
+            nl = fmx::fused2d_pol_supported(g->geo) ? fmx::launch_fused2d_pol(g->geo, c, a, g->stream)
+                                                    : fmx::launch_fused2d<T>(g->geo, c, a, g->stream);
+        } else {
+            nl = fmx::launch_fused2d<T>(g->geo, c, a, g->stream);
+        }
         if (nl < 0) return fail(FMX_EUNSUPPORTED, "fused 2D kernel: configuration not instantiated");
         g->launches += nl;
         g->cur = nxt;

@@ -37,4 +37,12 @@ struct Fused2dShape {
 template <typename T>
 Fused2dShape fused2d_shape(const Geo &g, int m, int passes);
 
+// FP32 path split by polarisation (fused2d_pol.cu): one TE and one TM launch
+// per step, two columns per thread, packed FP32x2 arithmetic.  Needs an even
+// n_x (column pairs never straddle the periodic seam).  Returns the number
+// of kernels launched or -1.
+bool fused2d_pol_supported(const Geo &g);
+int launch_fused2d_pol(const Geo &g, const Coef<float> &c, const Fused2dArgs<float> &a, cudaStream_t s);
+Fused2dShape fused2d_pol_shape(const Geo &g, int m, int passes);
+
 }  // namespace fmx

@@ -1,0 +1,544 @@
+// FP32 fused 2D step split by polarisation, two columns per thread.
+//
+// In 2D the scheme decouples exactly into the TE set (Ex, Ey, Bz; jx, jy)
+// and the TM set (Ez, Bx, By; jz) (Sec. 2.2.2: E_z is solved independently
+// of E_x and E_y, and Eqs. faraday_x_2d..ampere_aux_z_2d couple nothing
+// across the two sets).  Each set gets its own kernel; one step is one TE
+// launch and one TM launch.  Each kernel keeps the row pipeline of
+// fused2d.cu (J -> B prep -> source -> M sweeps -> E update -> Faraday, each
+// stage two rows behind its producer, one __syncthreads per row) but a
+// thread owns two adjacent columns and does the arithmetic on column pairs
+// with packed FP32x2 instructions.  Ring slots are compile-time constants: the
+// row loop runs in blocks of four rows from a row index that is a multiple of
+// four.  HBM traffic per cell and step: TE reads 5 and writes 3 FP32 values,
+// TM reads 4 and writes 3 (60 bytes together).
+#include <cuda_runtime.h>
+
+#include "fused2d.h"
+
+namespace fmx {
+namespace {
+
+typedef float2 f2;
+
+__device__ __forceinline__ f2 mk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ f2 add(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 mul(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+
+// coefficient pairs (both lanes equal), kept in the kernel's parameter space
+struct Coef2 {
+    f2 kx, ky, q, c6, ax, ay, axy, bxy;
+    f2 m1, m2;      // (-1, -1), (-2, -2)
+    f2 w[7];        // binomial weights of the x/y filter
+};
+
+__host__ __device__ constexpr double binom_w2(int P, int k) {
+    double c = 1.0;
+    for (int i = 0; i < k; ++i) c = c * (2 * P - i) / (i + 1);
+    double d = 1.0;
+    for (int i = 0; i < P; ++i) d *= 4.0;
+    return c / d;
+}
+
+enum { TE = 0, TM = 1 };
+
+template <int M, int P, bool HJ>
+struct PolGeom {
+    static constexpr int PX = (HJ && P > 1) ? P : 1;            // columns of x-reach of the source
+    static constexpr int HC = ((PX + M) + 1) / 2 * 2;           // left halo, even
+    static constexpr int PADP = (HJ && P > 1) ? (P + 1) / 2 : 1; // smem pad, in pairs
+    static constexpr int D0 = 12;                               // dE' ring depth (>= 2M+1, multiple of 4)
+    static constexpr int NS = M > 1 ? M - 1 : 0;
+    static constexpr int TJ = HJ ? 2 * P + 1 : 1;
+    static constexpr int WU = TJ > 3 ? TJ : 3;
+    static_assert(2 * M + 1 <= D0, "dE' ring too shallow");
+};
+
+// number of smem rows (each NT + 2 PADP pairs) of one polarisation kernel
+template <int POL, int M, int P, bool HJ>
+__host__ __device__ constexpr int pol_rows() {
+    using G = PolGeom<M, P, HJ>;
+    // TE: jy[2][2], bz[4], dp[D0][2], sw[NS][4][2], e[2]
+    // TM: jy[2], bx[4], ay[2], dp[D0], sw[NS][4], e[2]
+    return POL == TE ? ((HJ ? 4 : 0) + 4 + G::D0 * 2 + G::NS * 8 + 2)
+                     : ((HJ ? 2 : 0) + 4 + 2 + G::D0 + G::NS * 4 + 2);
+}
+
+template <int POL, int M, int P, bool HJ, int NT>
+__global__ void __launch_bounds__(NT, 3)
+    k_pol2d(Fused2dArgs<float> a, Geo g, Coef2 c, int W, int L, int nstrip) {
+    using G = PolGeom<M, P, HJ>;
+    constexpr int HC = G::HC, PADP = G::PADP, D0 = G::D0, NS = G::NS, TJ = G::TJ;
+    constexpr int RP = NT + 2 * PADP;  // pairs per smem row
+    constexpr int NC = POL == TE ? 2 : 1;  // E components of the set
+    extern __shared__ __align__(16) unsigned char smraw[];
+    f2 *sm = reinterpret_cast<f2 *>(smraw);
+    f2 *s_jy = sm;                                     // [2][NC][RP]
+    f2 *s_b0 = s_jy + (HJ ? 2 * NC * RP : 0);          // [4][RP]  TE: Bz, TM: Bx
+    f2 *s_ay = s_b0 + 4 * RP;                          // [2][RP]  TM only: alpha_y By
+    f2 *s_dp = s_ay + (POL == TM ? 2 * RP : 0);        // [D0][NC][RP]
+    f2 *s_sw = s_dp + D0 * NC * RP;                    // [NS][4][NC][RP]
+    f2 *s_e = s_sw + NS * 4 * NC * RP;                 // [2][RP]  TE: Ey, TM: Ez of E^{n+1}
+    constexpr int total = pol_rows<POL, M, P, HJ>() * RP;
+
+    const int tid = threadIdx.x;
+    for (int q = tid; q < total; q += NT) sm[q] = mk(0.f, 0.f);
+
+    const int strip = blockIdx.x % nstrip, seg = blockIdx.x / nstrip;
+    const int x0 = strip * W;
+    const int y0 = seg * L;
+    const int y1 = min(y0 + L, g.ny);
+    const int cg = x0 - HC + 2 * tid;  // first column of the pair
+    int xc = cg % g.nx;
+    if (xc < 0) xc += g.nx;
+    const bool xout = 2 * tid >= HC && 2 * tid < HC + W && cg < g.nx;
+    const int pc = tid + PADP;  // pair index in an smem row
+    // scalar views of smem rows: column 2t-1 and 2t+2 of this thread
+    auto left = [&](const f2 *row) { return reinterpret_cast<const float *>(row)[2 * pc - 1]; };
+    auto right = [&](const f2 *row) { return reinterpret_cast<const float *>(row)[2 * pc + 2]; };
+
+    // inputs of the set
+    const float *__restrict__ inJ0 = POL == TE ? a.J[0] : a.J[2];
+    const float *__restrict__ inJ1 = a.J[1];
+    const float *__restrict__ inB0 = POL == TE ? a.B[2] : a.B[0];  // TE: Bz   TM: Bx
+    const float *__restrict__ inB1 = a.B[1];                        // TM: By
+    const float *__restrict__ inE0 = POL == TE ? a.E[0] : a.E[2];  // TE: Ex   TM: Ez
+    const float *__restrict__ inE1 = a.E[1];                        // TE: Ey
+    float *__restrict__ oE0 = POL == TE ? a.Eo[0] : a.Eo[2];
+    float *__restrict__ oE1 = a.Eo[1];
+    float *__restrict__ oB0 = POL == TE ? a.Bo[2] : a.Bo[0];
+    float *__restrict__ oB1 = a.Bo[1];
+
+    // first row, aligned down to a multiple of 4 (extra warm-up rows are harmless)
+    int r0 = y0 - M - G::WU - 1;
+    r0 -= ((r0 % 4) + 4) % 4;
+    int r1 = y1 + 2 * M + 1;
+    r1 += (4 - ((r1 - r0) % 4)) % 4;
+
+    // running row offsets (element index of (row, xc)) of the four input rows
+    const int64_t plane = (int64_t)g.ny * g.pitch;
+    auto row_off = [&](int r) {
+        int y = r % g.ny;
+        if (y < 0) y += g.ny;
+        return (int64_t)y * g.pitch + xc;
+    };
+    int64_t oj = row_off(r0 + 1 + P), ob = row_off(r0 + 2), oe = row_off(r0 - 2 * M), of = row_off(r0 - 2 * M - 1);
+    auto adv = [&](int64_t &o) {
+        o += g.pitch;
+        if (o >= plane) o -= plane;
+    };
+
+    // register state (pairs)
+    f2 jw[NC][TJ];
+    f2 byw[3];           // TM: By rows r+2, r+1, r
+    f2 bprev;            // TE: Bz row r-1   TM: alpha_x Bx row r-1
+    f2 win[M > 0 ? M : 1][NC][3];
+    f2 aux[M > 0 ? M : 1][3];  // TE: h = Dbar_x Ex (rows rho+1, rho)   TM: Dbar_xx Ez (rho+1, rho, rho-1)
+    f2 en[NC], enp[NC];
+    const f2 z2 = mk(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+#pragma unroll
+        for (int k = 0; k < TJ; ++k) jw[q][k] = z2;
+        en[q] = enp[q] = z2;
+    }
+    byw[0] = byw[1] = byw[2] = z2;
+    bprev = z2;
+#pragma unroll
+    for (int s = 0; s < (M > 0 ? M : 1); ++s) {
+#pragma unroll
+        for (int q = 0; q < NC; ++q) win[s][q][0] = win[s][q][1] = win[s][q][2] = z2;
+        aux[s][0] = aux[s][1] = aux[s][2] = z2;
+    }
+
+    auto ld2 = [&](const float *p, int64_t o) { return __ldg(reinterpret_cast<const float2 *>(p + o)); };
+    // inputs of two rows ahead, double-buffered by row parity: j (NC), B (TE: Bz;
+    // TM: Bx, By), E (NC), B again for the Faraday update
+    f2 pj0[2] = {z2, z2}, pj1[2] = {z2, z2}, pb0[2], pb1[2] = {z2, z2}, pe0[2], pe1[2] = {z2, z2}, pf0[2],
+       pf1[2] = {z2, z2};
+    auto issue = [&](int k) {
+        if (HJ) {
+            pj0[k] = ld2(inJ0, oj);
+            if (POL == TE) pj1[k] = ld2(inJ1, oj);
+        }
+        pb0[k] = ld2(inB0, ob);
+        if (POL == TM) pb1[k] = ld2(inB1, ob);
+        pe0[k] = ld2(inE0, oe);
+        if (POL == TE) pe1[k] = ld2(inE1, oe);
+        pf0[k] = ld2(inB0, of);
+        if (POL == TM) pf1[k] = ld2(inB1, of);
+    };
+    auto adv_all = [&]() {
+        adv(oj);
+        adv(ob);
+        adv(oe);
+        adv(of);
+    };
+    issue(0);  // row r0 (r0 is even)
+    adv_all();
+    issue(1);  // row r0 + 1
+    adv_all(); // offsets now point at row r0 + 2
+    int b0 = ((r0 % D0) + D0) % D0;  // dE' ring slot of row r0 (a multiple of 4)
+    __syncthreads();
+
+    for (int rb = r0; rb < r1; rb += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = rb + u;
+            const int k = u & 1;  // buffer of row r (compile-time)
+            const f2 cj0 = pj0[k], cj1 = pj1[k], cb0 = pb0[k], cb1 = pb1[k], ce0 = pe0[k], ce1 = pe1[k],
+                     cf0 = pf0[k], cf1 = pf1[k];
+            if (r + 2 < r1) issue(k);  // row r + 2
+            adv_all();
+            const int rhoM = r - 2 * M, rhoF = rhoM - 1;
+            // dE' ring slot of row r - k (u, k compile-time; b0 in {0, 4, 8})
+            auto dslot = [&](int k) {
+                int sl = b0 + u - k;
+                return sl < 0 ? sl + D0 : sl;
+            };
+
+            // ---------------- sweeps M..1 ----------------
+#pragma unroll
+            for (int s = M; s >= 1; --s) {
+                // rows of stage s-1: rho+1, rho, rho-1 (ring slots)
+                const f2 *rp1, *r0w, *rm1;
+                if (s == 1) {
+                    rp1 = s_dp + dslot(2 * s - 1) * NC * RP;
+                    r0w = s_dp + dslot(2 * s) * NC * RP;
+                    rm1 = s_dp + dslot(2 * s + 1) * NC * RP;
+                } else {
+                    const f2 *base = s_sw + (s - 2) * 4 * NC * RP;
+                    rp1 = base + ((u - 2 * s + 1 + 16) & 3) * NC * RP;
+                    r0w = base + ((u - 2 * s + 16) & 3) * NC * RP;
+                    rm1 = base + ((u - 2 * s - 1 + 16) & 3) * NC * RP;
+                }
+                const f2 *dp = s_dp + dslot(2 * s) * NC * RP;
+                f2 o0, o1 = z2;
+                if constexpr (POL == TE) {
+                    const f2 *X = win[s - 1][0];
+                    const f2 *Y = win[s - 1][1];
+                    // h = Dbar_x(bwd) Ex at row rho+1: X0 - (Ex[2t-1], X0.x)
+                    const float exl = left(rp1);
+                    aux[s - 1][1] = aux[s - 1][0];
+                    aux[s - 1][0] = fma(mk(exl, X[0].x), c.m1, X[0]);
+                    const float eyl = left(r0w + RP), eyr = right(r0w + RP), eyr_m = right(rm1 + RP);
+                    const f2 g_own = fma(Y[2], c.m1, Y[1]);
+                    const f2 g_nb = mk(g_own.y, eyr - eyr_m);
+                    const f2 dyyx = fma(X[1], c.m2, add(X[0], X[2]));
+                    const f2 dxxy = fma(Y[1], c.m2, add(mk(eyl, Y[1].x), mk(Y[1].y, eyr)));
+                    o0 = fma(c.ay, dyyx, dp[pc]);
+                    o0 = fma(c.bxy, fma(g_own, c.m1, g_nb), o0);
+                    o1 = fma(c.ax, dxxy, dp[RP + pc]);
+                    o1 = fma(c.bxy, fma(aux[s - 1][1], c.m1, aux[s - 1][0]), o1);
+                } else {
+                    const f2 *Z = win[s - 1][0];
+                    const float ezl = left(rp1), ezr = right(rp1);
+                    aux[s - 1][2] = aux[s - 1][1];
+                    aux[s - 1][1] = aux[s - 1][0];
+                    aux[s - 1][0] = fma(Z[0], c.m2, add(mk(ezl, Z[0].x), mk(Z[0].y, ezr)));
+                    const f2 *D = aux[s - 1];
+                    const f2 dyy = fma(Z[1], c.m2, add(Z[0], Z[2]));
+                    const f2 dxxyy = fma(D[1], c.m2, add(D[0], D[2]));
+                    o0 = fma(c.ax, D[1], dp[pc]);
+                    o0 = fma(c.ay, dyy, o0);
+                    o0 = fma(c.axy, dxxyy, o0);
+                }
+                if (s < M) {
+                    f2 *o = s_sw + (s - 1) * 4 * NC * RP + ((u - 2 * s + 16) & 3) * NC * RP;
+                    o[pc] = o0;
+                    if (POL == TE) o[RP + pc] = o1;
+#pragma unroll
+                    for (int q = 0; q < NC; ++q) {
+                        win[s][q][2] = win[s][q][1];
+                        win[s][q][1] = win[s][q][0];
+                    }
+                    win[s][0][0] = o0;
+                    if (POL == TE) win[s][1][0] = o1;
+                } else {
+                    // ---------------- E update (row rhoM) and Faraday (row rhoF) ----------------
+                    enp[0] = en[0];
+                    en[0] = add(ce0, o0);
+                    if (POL == TE) {
+                        enp[1] = en[1];
+                        en[1] = add(ce1, o1);
+                    }
+                    const bool yE = rhoM >= y0 && rhoM < y1;
+                    if (yE && xout) {
+                        const int64_t o = (int64_t)rhoM * g.pitch + xc;
+                        *reinterpret_cast<float2 *>(oE0 + o) = en[0];
+                        if (POL == TE) *reinterpret_cast<float2 *>(oE1 + o) = en[1];
+                    }
+                    f2 *se = s_e + (u & 1) * RP;
+                    se[pc] = POL == TE ? en[1] : en[0];
+                    const f2 *sf = s_e + ((u + 1) & 1) * RP;  // row rhoF
+                    const float er = right(sf);
+                    f2 bo0, bo1 = z2;
+                    if constexpr (POL == TE) {
+                        // Bz -= kx (Ey[i+1] - Ey[i]) - ky (Ex[j+1] - Ex[j])
+                        const f2 dxey = fma(enp[1], c.m1, mk(enp[1].y, er));
+                        const f2 dyex = fma(enp[0], c.m1, en[0]);
+                        bo0 = fma(c.ky, dyex, fma(fma(c.kx, dxey, z2), c.m1, cf0));
+                    } else {
+                        // Bx -= ky (Ez[j+1] - Ez[j]);  By += kx (Ez[i+1] - Ez[i])
+                        const f2 dyez = fma(enp[0], c.m1, en[0]);
+                        const f2 dxez = fma(enp[0], c.m1, mk(enp[0].y, er));
+                        bo0 = fma(fma(c.ky, dyez, z2), c.m1, cf0);
+                        bo1 = fma(c.kx, dxez, cf1);
+                    }
+                    const bool yF = rhoF >= y0 && rhoF < y1;
+                    if (yF && xout) {
+                        const int64_t o = (int64_t)rhoF * g.pitch + xc;
+                        *reinterpret_cast<float2 *>(oB0 + o) = bo0;
+                        if (POL == TM) *reinterpret_cast<float2 *>(oB1 + o) = bo1;
+                    }
+                }
+            }
+
+            // ---------------- source, row r ----------------
+            {
+                f2 jf0 = z2, jf1 = z2;
+                if (HJ) {
+                    const f2 *jr = s_jy + (u & 1) * NC * RP;
+#pragma unroll
+                    for (int q = 0; q < NC; ++q) {
+                        const f2 *row = jr + q * RP;
+                        // columns 2t-P .. 2t+1+P as shifted pairs of the loaded pairs
+                        f2 acc = z2;
+                        if (P == 0) {
+                            acc = row[pc];
+                        } else {
+                            const float *sr = reinterpret_cast<const float *>(row);
+#pragma unroll
+                            for (int k = 0; k <= 2 * P; ++k) {
+                                const int cidx = 2 * pc - P + k;
+                                const f2 v = (((k - P) & 1) == 0) ? row[pc + (k - P) / 2]
+                                                                   : mk(sr[cidx], sr[cidx + 1]);
+                                acc = fma(c.w[k], v, acc);
+                            }
+                        }
+                        if (q == 0) jf0 = acc; else jf1 = acc;
+                    }
+                }
+                f2 d0, d1 = z2;
+                if constexpr (POL == TE) {
+                    const f2 *sb = s_b0 + (u & 3) * RP;
+                    const f2 bz0 = sb[pc];
+                    const float bzl = left(sb);
+                    // dE'_x = ky (Bz[j] - Bz[j-1]) - q jx ;  dE'_y = -kx (Bz[i] - Bz[i-1]) - q jy
+                    d0 = mul(c.ky, fma(bprev, c.m1, bz0));
+                    d1 = mul(c.kx, fma(bz0, c.m1, mk(bzl, bz0.x)));
+                    bprev = bz0;
+                    if (HJ) {
+                        d0 = fma(c.q, fma(jf0, c.m1, z2), d0);
+                        d1 = fma(c.q, fma(jf1, c.m1, z2), d1);
+                    }
+                } else {
+                    const f2 *sb = s_b0 + (u & 3) * RP;
+                    const f2 bx0 = sb[pc];
+                    const f2 axbx = fma(c.c6, fma(bx0, c.m2, add(mk(left(sb), bx0.x), mk(bx0.y, right(sb)))), bx0);
+                    const f2 *sa = s_ay + (u & 1) * RP;
+                    const f2 ay0 = sa[pc];
+                    const f2 dxay = fma(mk(left(sa), ay0.x), c.m1, ay0);
+                    // dE'_z = kx Dbar_x(alpha_y By) - ky Dbar_y(alpha_x Bx) - q jz
+                    d0 = fma(c.kx, dxay, mul(fma(c.ky, fma(bprev, c.m1, axbx), z2), c.m1));
+                    bprev = axbx;
+                    if (HJ) d0 = fma(c.q, fma(jf0, c.m1, z2), d0);
+                }
+                f2 *dp = s_dp + dslot(0) * NC * RP;
+                dp[pc] = d0;
+                if (POL == TE) dp[RP + pc] = d1;
+                if (M > 0) {
+#pragma unroll
+                    for (int q = 0; q < NC; ++q) {
+                        win[0][q][2] = win[0][q][1];
+                        win[0][q][1] = win[0][q][0];
+                    }
+                    win[0][0][0] = d0;
+                    if (POL == TE) win[0][1][0] = d1;
+                } else {
+                    // no sweeps: dE = dE'
+                    enp[0] = en[0];
+                    en[0] = add(ce0, d0);
+                    if (POL == TE) {
+                        enp[1] = en[1];
+                        en[1] = add(ce1, d1);
+                    }
+                    const bool yE = rhoM >= y0 && rhoM < y1;
+                    if (yE && xout) {
+                        const int64_t o = (int64_t)rhoM * g.pitch + xc;
+                        *reinterpret_cast<float2 *>(oE0 + o) = en[0];
+                        if (POL == TE) *reinterpret_cast<float2 *>(oE1 + o) = en[1];
+                    }
+                    f2 *se = s_e + (u & 1) * RP;
+                    se[pc] = POL == TE ? en[1] : en[0];
+                    const f2 *sf = s_e + ((u + 1) & 1) * RP;
+                    const float er = right(sf);
+                    f2 bo0, bo1 = z2;
+                    if constexpr (POL == TE) {
+                        const f2 dxey = fma(enp[1], c.m1, mk(enp[1].y, er));
+                        const f2 dyex = fma(enp[0], c.m1, en[0]);
+                        bo0 = fma(c.ky, dyex, fma(fma(c.kx, dxey, z2), c.m1, cf0));
+                    } else {
+                        const f2 dyez = fma(enp[0], c.m1, en[0]);
+                        const f2 dxez = fma(enp[0], c.m1, mk(enp[0].y, er));
+                        bo0 = fma(fma(c.ky, dyez, z2), c.m1, cf0);
+                        bo1 = fma(c.kx, dxez, cf1);
+                    }
+                    const bool yF = rhoF >= y0 && rhoF < y1;
+                    if (yF && xout) {
+                        const int64_t o = (int64_t)rhoF * g.pitch + xc;
+                        *reinterpret_cast<float2 *>(oB0 + o) = bo0;
+                        if (POL == TM) *reinterpret_cast<float2 *>(oB1 + o) = bo1;
+                    }
+                }
+            }
+
+            // ---------------- current: y-binomial of row r+1 ----------------
+            if (HJ) {
+                f2 *jo = s_jy + ((u + 1) & 1) * NC * RP;
+#pragma unroll
+                for (int q = 0; q < NC; ++q) {
+#pragma unroll
+                    for (int k = TJ - 1; k > 0; --k) jw[q][k] = jw[q][k - 1];
+                    jw[q][0] = q == 0 ? cj0 : cj1;
+                    f2 acc = mul(c.w[0], jw[q][0]);
+#pragma unroll
+                    for (int k = 1; k < TJ; ++k) acc = fma(c.w[k], jw[q][k], acc);
+                    jo[q * RP + pc] = acc;
+                }
+            }
+
+            // ---------------- B prep, row r+2 ----------------
+            {
+                s_b0[((u + 2) & 3) * RP + pc] = cb0;
+                if (POL == TM) {
+                    byw[2] = byw[1];
+                    byw[1] = byw[0];
+                    byw[0] = cb1;
+                    s_ay[((u + 1) & 1) * RP + pc] = fma(c.c6, fma(byw[1], c.m2, add(byw[0], byw[2])), byw[1]);
+                }
+            }
+            __syncthreads();
+        }
+        b0 += 4;
+        if (b0 >= D0) b0 -= D0;
+    }
+}
+
+template <int POL, int M, int P, bool HJ>
+struct PolLauncher {
+    static constexpr int NT = 128;
+    static size_t smem_bytes() { return (size_t)pol_rows<POL, M, P, HJ>() * (NT + 2 * PolGeom<M, P, HJ>::PADP) * 8; }
+    static int blocks_per_sm() {
+        static int b = -1;
+        if (b < 0) {
+            auto k = k_pol2d<POL, M, P, HJ, NT>;
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes());
+            int n = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, NT, smem_bytes()) != cudaSuccess || n < 1) n = 1;
+            b = n;
+        }
+        return b;
+    }
+    static Fused2dShape shape(const Geo &g) {
+        using Gm = PolGeom<M, P, HJ>;
+        Fused2dShape sh;
+        sh.threads = NT;
+        sh.halo = Gm::HC;
+        sh.width = 2 * NT - 2 * Gm::HC - 2;
+        sh.strips = (g.nx + sh.width - 1) / sh.width;
+        static int sms = -1;
+        if (sms < 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+        }
+        const int target = blocks_per_sm() * sms;
+        int nseg = target / sh.strips;
+        if (nseg < 1) nseg = 1;
+        if (nseg > g.ny) nseg = g.ny;
+        sh.rows = (g.ny + nseg - 1) / nseg;
+        sh.segments = (g.ny + sh.rows - 1) / sh.rows;
+        return sh;
+    }
+    static void run(const Geo &g, const Coef2 &c, const Fused2dArgs<float> &a, cudaStream_t s) {
+        const Fused2dShape sh = shape(g);
+        k_pol2d<POL, M, P, HJ, NT><<<sh.strips * sh.segments, NT, smem_bytes(), s>>>(a, g, c, sh.width, sh.rows,
+                                                                                    sh.strips);
+    }
+};
+
+template <int M, int P, bool HJ>
+int run_both(const Geo &g, const Coef2 &c, const Fused2dArgs<float> &a, cudaStream_t s, Fused2dShape *sh) {
+    if (sh) {
+        *sh = PolLauncher<TE, M, P, HJ>::shape(g);
+        return 0;
+    }
+    PolLauncher<TE, M, P, HJ>::run(g, c, a, s);
+    PolLauncher<TM, M, P, HJ>::run(g, c, a, s);
+    return 2;
+}
+
+template <int M>
+int pol_p(const Geo &g, const Coef2 &c, const Fused2dArgs<float> &a, cudaStream_t s, bool hj, int p,
+          Fused2dShape *sh) {
+    if (!hj) return run_both<M, 0, false>(g, c, a, s, sh);
+    switch (p) {
+        case 0: return run_both<M, 0, true>(g, c, a, s, sh);
+        case 1: return run_both<M, 1, true>(g, c, a, s, sh);
+        case 2: return run_both<M, 2, true>(g, c, a, s, sh);
+        case 3: return run_both<M, 3, true>(g, c, a, s, sh);
+    }
+    return -1;
+}
+
+int pol_dispatch(const Geo &g, const Coef2 &c, const Fused2dArgs<float> &a, cudaStream_t s, int m, bool hj, int p,
+                 Fused2dShape *sh) {
+    switch (m) {
+        case 0: return pol_p<0>(g, c, a, s, hj, p, sh);
+        case 1: return pol_p<1>(g, c, a, s, hj, p, sh);
+        case 2: return pol_p<2>(g, c, a, s, hj, p, sh);
+        case 3: return pol_p<3>(g, c, a, s, hj, p, sh);
+        case 4: return pol_p<4>(g, c, a, s, hj, p, sh);
+    }
+    return -1;
+}
+
+Coef2 make_coef2(const Coef<float> &c, int passes) {
+    auto b = [](float v) { return make_float2(v, v); };
+    Coef2 k;
+    k.kx = b(c.kx);
+    k.ky = b(c.ky);
+    k.q = b(c.q);
+    k.c6 = b(c.c6);
+    k.ax = b(c.ax);
+    k.ay = b(c.ay);
+    k.axy = b(c.axy);
+    k.bxy = b(c.bxy);
+    k.m1 = b(-1.f);
+    k.m2 = b(-2.f);
+    for (int i = 0; i < 7; ++i) k.w[i] = b(i <= 2 * passes ? (float)binom_w2(passes, i) : 0.f);
+    return k;
+}
+
+}  // namespace
+
+bool fused2d_pol_supported(const Geo &g) { return g.nx % 2 == 0; }
+
+int launch_fused2d_pol(const Geo &g, const Coef<float> &c, const Fused2dArgs<float> &a, cudaStream_t s) {
+    const bool hj = a.J[0] != nullptr;
+    const int p = hj ? a.passes : 0;
+    return pol_dispatch(g, make_coef2(c, p), a, s, a.m, hj, p, nullptr);
+}
+
+Fused2dShape fused2d_pol_shape(const Geo &g, int m, int passes) {
+    Fused2dShape sh{0, 0, 0, 0, 0, 0};
+    Fused2dArgs<float> a{};
+    Coef<float> c{};
+    pol_dispatch(g, make_coef2(c, passes >= 0 ? passes : 0), a, nullptr, m, passes >= 0, passes >= 0 ? passes : 0,
+                 &sh);
+    return sh;
+}
+
+}  // namespace fmx

@@ -87,6 +87,31 @@ def test_fused_fp64_every_instantiation(fmx, m, passes):
     assert_parity(Eg, Bg, Eo, Bo, TOL64, f"fused m={m} p={passes}")
 
 
+@pytest.mark.parametrize("m", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("passes", [0, 1, 2, 3, None])
+def test_fused_fp32_every_instantiation(fmx, m, passes):
+    """FP32 fused path: the polarisation-split kernels (even n_x) and the
+    single-kernel path (odd n_x), every (m, passes) pair, several strips and
+    segments, against the oracle with FP32-rounded coefficients."""
+    for shape in ((262, 97), (261, 97)):
+        E, B, J = _inputs(shape, 200 + m, np.float32, with_j=passes is not None, smooth=True)
+        p = passes or 0
+        Eg, Bg, _ = _run_gpu(fmx, shape, E, B, J, 7, precision=0, m=m, filter_passes=p, engine=2, courant=0.8)
+        Eo, Bo, rc, _ = _oracle(shape, E.astype(np.float64), B.astype(np.float64),
+                                None if J is None else J.astype(np.float64), 7, m=m, filter_passes=p, courant=0.8,
+                                coef_f32=True)
+        assert_parity(Eg, Bg, Eo, Bo, TOL32, f"fused fp32 {shape} m={m} p={passes}")
+
+
+@pytest.mark.parametrize("shape", [(2, 2), (4, 3), (2, 9), (600, 2), (1030, 6)])
+def test_fused_fp32_small_and_thin(fmx, shape):
+    E, B, J = _inputs(shape, 301, np.float32)
+    Eg, Bg, _ = _run_gpu(fmx, shape, E, B, J, 5, precision=0, m=4, filter_passes=3, engine=2)
+    Eo, Bo, rc, _ = _oracle(shape, E.astype(np.float64), B.astype(np.float64), J.astype(np.float64), 5, m=4,
+                            filter_passes=3, coef_f32=True)
+    assert_parity(Eg, Bg, Eo, Bo, TOL32, f"fp32 thin {shape}")
+
+
 @pytest.mark.parametrize("shape", [(13, 11, 7), (9, 8, 6), (40,), (17, 1, 5)])
 def test_staged_fp64_3d_1d(fmx, shape):
     E, B, J = _inputs(shape, 31, np.float64)
@@ -194,7 +219,7 @@ def test_full_size_4096_windows(fmx, nsteps):
                 e = rel_l2(Fw[c][sl[1:]], F_o[c][sl[1:]])
                 worst = max(worst, e)
                 assert e < TOL32, (cy, cx, c, e)
-    assert g.launches == nsteps
+    assert g.launches == 2 * nsteps  # one TE and one TM launch per step
 
 
 # ---------------------------------------------------------------------------
