@@ -43,6 +43,12 @@ __host__ __device__ constexpr double binom_w2(int P, int k) {
 
 enum { TE = 0, TM = 1 };
 
+// rows of input prefetch held in registers (divides 4)
+template <int POL>
+struct PolPrefetch {
+    static constexpr int PD = 2;
+};
+
 template <int M, int P, bool HJ>
 struct PolGeom {
     static constexpr int PX = (HJ && P > 1) ? P : 1;            // columns of x-reach of the source
@@ -153,10 +159,13 @@ __global__ void __launch_bounds__(NT, 3)
     }
 
     auto ld2 = [&](const float *p, int64_t o) { return __ldg(reinterpret_cast<const float2 *>(p + o)); };
-    // inputs of two rows ahead, double-buffered by row parity: j (NC), B (TE: Bz;
-    // TM: Bx, By), E (NC), B again for the Faraday update
-    f2 pj0[2] = {z2, z2}, pj1[2] = {z2, z2}, pb0[2], pb1[2] = {z2, z2}, pe0[2], pe1[2] = {z2, z2}, pf0[2],
-       pf1[2] = {z2, z2};
+    // inputs of PD rows ahead, one buffer per row modulo PD (PD divides the
+    // four-row unroll, so the buffer of a row is a compile-time constant):
+    // j (NC), B (TE: Bz; TM: Bx, By), E (NC), B again for the Faraday update
+    constexpr int PD = PolPrefetch<POL>::PD;
+    f2 pj0[PD], pj1[PD], pb0[PD], pb1[PD], pe0[PD], pe1[PD], pf0[PD], pf1[PD];
+#pragma unroll
+    for (int k = 0; k < PD; ++k) pj0[k] = pj1[k] = pb0[k] = pb1[k] = pe0[k] = pe1[k] = pf0[k] = pf1[k] = z2;
     auto issue = [&](int k) {
         if (HJ) {
             pj0[k] = ld2(inJ0, oj);
@@ -175,10 +184,11 @@ __global__ void __launch_bounds__(NT, 3)
         adv(oe);
         adv(of);
     };
-    issue(0);  // row r0 (r0 is even)
-    adv_all();
-    issue(1);  // row r0 + 1
-    adv_all(); // offsets now point at row r0 + 2
+#pragma unroll
+    for (int k = 0; k < PD; ++k) {  // rows r0 .. r0 + PD - 1 (r0 is a multiple of 4)
+        issue(k);
+        adv_all();
+    }
     int b0 = ((r0 % D0) + D0) % D0;  // dE' ring slot of row r0 (a multiple of 4)
     __syncthreads();
 
@@ -186,10 +196,10 @@ __global__ void __launch_bounds__(NT, 3)
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int r = rb + u;
-            const int k = u & 1;  // buffer of row r (compile-time)
+            const int k = u % PD;  // buffer of row r (compile-time)
             const f2 cj0 = pj0[k], cj1 = pj1[k], cb0 = pb0[k], cb1 = pb1[k], ce0 = pe0[k], ce1 = pe1[k],
                      cf0 = pf0[k], cf1 = pf1[k];
-            if (r + 2 < r1) issue(k);  // row r + 2
+            if (r + PD < r1) issue(k);  // row r + PD
             adv_all();
             const int rhoM = r - 2 * M, rhoF = rhoM - 1;
             // dE' ring slot of row r - k (u, k compile-time; b0 in {0, 4, 8})
@@ -303,19 +313,19 @@ __global__ void __launch_bounds__(NT, 3)
 #pragma unroll
                     for (int q = 0; q < NC; ++q) {
                         const f2 *row = jr + q * RP;
-                        // columns 2t-P .. 2t+1+P as shifted pairs of the loaded pairs
-                        f2 acc = z2;
-                        if (P == 0) {
-                            acc = row[pc];
-                        } else {
-                            const float *sr = reinterpret_cast<const float *>(row);
+                        // aligned pairs pc-H .. pc+H cover columns 2t-P .. 2t+1+P; the
+                        // odd-shifted tap pairs are assembled from them in registers
+                        constexpr int H = (P + 1) / 2;
+                        f2 pr[2 * H + 1];
 #pragma unroll
-                            for (int k = 0; k <= 2 * P; ++k) {
-                                const int cidx = 2 * pc - P + k;
-                                const f2 v = (((k - P) & 1) == 0) ? row[pc + (k - P) / 2]
-                                                                   : mk(sr[cidx], sr[cidx + 1]);
-                                acc = fma(c.w[k], v, acc);
-                            }
+                        for (int d = -H; d <= H; ++d) pr[d + H] = row[pc + d];
+                        f2 acc = z2;
+#pragma unroll
+                        for (int k = 0; k <= 2 * P; ++k) {
+                            const int off = k - P;  // column offset of the tap
+                            const int lo = (off - 1) / 2;  // for odd off, pair t+lo holds column 2t+off
+                            const f2 v = (off & 1) == 0 ? pr[H + off / 2] : mk(pr[H + lo].y, pr[H + lo + 1].x);
+                            acc = k == 0 ? mul(c.w[0], v) : fma(c.w[k], v, acc);
                         }
                         if (q == 0) jf0 = acc; else jf1 = acc;
                     }
