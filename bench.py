@@ -67,16 +67,16 @@ def _peaks():
 
 def _kernel_hash():
     h = hashlib.sha256()
-    for name in ("fused2d.cu", "fused2d.h", "fmx_internal.h"):
+    for name in ("fused2d_pol.cu", "fused2d.h", "fmx_internal.h"):
         with open(os.path.join(ROOT, "paper_1907_13088_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic():
-    """dram bytes per launch of the fused kernel from the committed ncu
+def _ncu_traffic(kernel_name):
+    """dram bytes (read + write) per launch of a kernel from the committed ncu
     summary, or None when absent or taken on another version of the kernel."""
-    path = os.path.join(ROOT, "profiles", "fused2d_4096_traffic.json")
+    path = os.path.join(ROOT, "profiles", "fused2d_pol_4096_traffic.json")
     if not os.path.exists(path):
         return None
     try:
@@ -84,7 +84,7 @@ def _ncu_traffic():
             d = json.load(f)
         if d.get("kernel_sha256_16") != _kernel_hash():
             return None
-        return float(d["dram_bytes_per_launch"])
+        return float(d["dram_bytes_per_launch"][kernel_name])
     except Exception:
         return None
 
@@ -237,26 +237,41 @@ def run_ours(args):
         dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
     e2e_value = world * cells * e2e_steps / float(e2e_s.item()) / 1e9
 
+    # per-kernel durations, CUDA events on the launching stream, after the timed region
+    prof_steps = max(50, min(500, args.steps))
+    g.profile(True)
+    g.step(prof_steps)
+    kstats = g.profile_read()
+    g.profile(False)
+
     cpu = cpu_baseline(E, B, J) if (rank == 0 and args.cpu_baseline) else None
 
     if rank == 0:
         value = world * cells * args.steps / (ms_max / 1e3) / 1e9
-        per_launch_s = (ms / 1e3) / args.steps
-        achieved = BYTES_PER_CELL * cells / per_launch_s / 1e9
         peak, peak_src = _peaks()
-        traffic = _ncu_traffic()
+        dom = max(kstats, key=lambda k: k["total_ms"])
+        per_launch_s = dom["total_ms"] / 1e3 / dom["launches"]
+        achieved = dom["bytes_per_launch"] / per_launch_s / 1e9
+        step_s = (ms / 1e3) / args.steps
+        kernels = [{"name": k["name"], "ms_per_launch": round(k["total_ms"] / k["launches"], 5),
+                    "algorithmic_bytes_per_launch": k["bytes_per_launch"],
+                    "achieved_gbs": round(k["bytes_per_launch"] / (k["total_ms"] / 1e3 / k["launches"]) / 1e9, 1),
+                    "ncu_dram_bytes_per_launch": _ncu_traffic(k["name"])} for k in kstats]
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 6), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": [NX, NY], "cells_per_gpu": cells, "m": M_SWEEPS,
-                       "filter_passes": PASSES, "courant": COURANT, "engine": "fused2d",
+                       "filter_passes": PASSES, "courant": COURANT, "engine": "fused2d (TE + TM kernels)",
                        "l2": "inputs larger than L2 (1.0 GB of fields per step vs 129 MB L2)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "peak_source": peak_src, "bytes_per_cell_step": BYTES_PER_CELL,
-                         "kernel": "k_fused2d<float,4,3,true,256>"},
+                         "frac": round(achieved / peak, 4), "traffic": _ncu_traffic(dom["name"]),
+                         "kernel": dom["name"], "peak_source": peak_src,
+                         "bytes_per_cell_step": BYTES_PER_CELL,
+                         "step": {"achieved": round(BYTES_PER_CELL * cells / step_s / 1e9, 1),
+                                  "frac": round(BYTES_PER_CELL * cells / step_s / 1e9 / peak, 4)},
+                         "kernels": kernels, "timing": f"CUDA events around each launch, {prof_steps} steps"},
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": 9 * 4 * cells,
                     "d2h_bytes_per_step": 6 * 4 * cells, "steps": e2e_steps,

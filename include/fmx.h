@@ -217,6 +217,22 @@ void *fmx_field_ptr(const fmx_grid *g, int c);
 /* Number of device kernels this grid has launched since fmx_bind. */
 int64_t fmx_launch_count(const fmx_grid *g);
 
+/* Per-kernel timing of the fused engine: while enabled, every kernel of
+ * fmx_step is bracketed by CUDA events recorded on the grid's stream.
+ * fmx_profile_read synchronises, returns one record per kernel kind (the
+ * launches, their summed event time, and the algorithmic HBM bytes one
+ * launch must move: 4 or 8 bytes per value read or written once) and clears
+ * the records.  Not part of the paper; used to measure each kernel against
+ * the HBM roofline.  Errors: FMX_ESTATE (not bound), FMX_ECUDA. */
+typedef struct {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+    double bytes_per_launch;
+} fmx_kernel_stat;
+fmx_status fmx_profile_enable(fmx_grid *g, int enable);
+fmx_status fmx_profile_read(fmx_grid *g, fmx_kernel_stat *out, int max, int *n);
+
 /* Size of the device scratch array behind fmx_step_static (4 MiB). */
 #define FMX_STATIC_SCRATCH_BYTES (4u << 20)
 

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "fmx.h"
 #include "fmx_internal.h"
@@ -172,6 +173,11 @@ struct fmx_grid {
     int64_t nparts = 0;
     double *diag_out = nullptr;
     fmx::DevStatus *st = nullptr;
+    // per-kernel timing (fmx_profile_enable): events of each profiled step
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;  // reused across reads
+    size_t ev_used = 0;
+    int prof_kinds = 0;                // events per step - 1
     // counters
     int64_t steps = 0, total_sweeps = 0, launches = 0;
     int last_sweeps = 0;
@@ -328,6 +334,18 @@ fmx_status staged_step(fmx_grid *g) {
     return FMX_OK;
 }
 
+// Next n events of the profiling pool (created on first use, then reused).
+cudaEvent_t *profile_events(fmx_grid *g, size_t n) {
+    while (g->ev_pool.size() < g->ev_used + n) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        g->ev_pool.push_back(e);
+    }
+    cudaEvent_t *p = g->ev_pool.data() + g->ev_used;
+    g->ev_used += n;
+    return p;
+}
+
 template <typename T>
 fmx_status fused_step(fmx_grid *g, int nsteps) {
     const fmx::Coef<T> c = make_coef<T>(g->co);
@@ -343,12 +361,23 @@ fmx_status fused_step(fmx_grid *g, int nsteps) {
         }
         a.m = g->p.m;
         a.passes = (g->p.filter_target == FMX_FILTER_CURRENT && g->buf.J[0]) ? g->p.filter_passes : 0;
+        cudaEvent_t *ev = g->prof ? profile_events(g, 3) : nullptr;
         int nl;
         if constexpr (sizeof(T) == 4) {
-            nl = fmx::fused2d_pol_supported(g->geo) ? fmx::launch_fused2d_pol(g->geo, c, a, g->stream)
-                                                    : fmx::launch_fused2d<T>(g->geo, c, a, g->stream);
+            if (fmx::fused2d_pol_supported(g->geo)) {
+                nl = fmx::launch_fused2d_pol(g->geo, c, a, g->stream, ev);
+                g->prof_kinds = 2;
+            } else {
+                if (ev) cudaEventRecord(ev[0], g->stream);
+                nl = fmx::launch_fused2d<T>(g->geo, c, a, g->stream);
+                if (ev) cudaEventRecord(ev[1], g->stream), cudaEventRecord(ev[2], g->stream);
+                g->prof_kinds = 1;
+            }
         } else {
+            if (ev) cudaEventRecord(ev[0], g->stream);
             nl = fmx::launch_fused2d<T>(g->geo, c, a, g->stream);
+            if (ev) cudaEventRecord(ev[1], g->stream), cudaEventRecord(ev[2], g->stream);
+            g->prof_kinds = 1;
         }
         if (nl < 0) return fail(FMX_EUNSUPPORTED, "fused 2D kernel: configuration not instantiated");
         g->launches += nl;
@@ -617,7 +646,67 @@ void *fmx_field_ptr(const fmx_grid *g, int c) {
 
 int64_t fmx_launch_count(const fmx_grid *g) { return g ? g->launches : 0; }
 
-void fmx_destroy(fmx_grid *g) { delete g; }
+fmx_status fmx_profile_enable(fmx_grid *g, int enable) {
+    if (!g) return fail(FMX_EINVAL, "NULL grid");
+    if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
+    if (g->engine != FMX_ENGINE_FUSED) return fail(FMX_EUNSUPPORTED, "per-kernel timing covers the fused engine");
+    g->prof = enable != 0;
+    return FMX_OK;
+}
+
+fmx_status fmx_profile_read(fmx_grid *g, fmx_kernel_stat *out, int max, int *n) {
+    if (!g || !out || !n) return fail(FMX_EINVAL, "NULL argument");
+    if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
+    *n = 0;
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    const int kinds = g->prof_kinds;
+    if (kinds == 0 || g->ev_used == 0) {
+        g->ev_used = 0;
+        return FMX_OK;
+    }
+    const double cells = (double)g->geo.nx * g->geo.ny * g->geo.nz;
+    const bool hj = g->buf.J[0] != nullptr;
+    const double esz = (double)g->elem;
+    const char *names[2];
+    double bytes[2];
+    if (kinds == 2) {
+        names[0] = "k_pol2d TE (Ex, Ey, Bz)";
+        names[1] = "k_pol2d TM (Ez, Bx, By)";
+        bytes[0] = cells * esz * ((hj ? 5 : 3) + 3);
+        bytes[1] = cells * esz * ((hj ? 4 : 3) + 3);
+    } else {
+        names[0] = "k_fused2d";
+        bytes[0] = cells * esz * ((hj ? 9 : 6) + 6);
+    }
+    double tot[2] = {0.0, 0.0};
+    const size_t steps = g->ev_used / 3;
+    for (size_t k = 0; k < steps; ++k) {
+        cudaEvent_t *ev = g->ev_pool.data() + 3 * k;
+        for (int q = 0; q < kinds; ++q) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, ev[q], ev[q + 1]);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+            tot[q] += ms;
+        }
+    }
+    for (int q = 0; q < kinds && q < max; ++q) {
+        memset(&out[q], 0, sizeof(out[q]));
+        snprintf(out[q].name, sizeof(out[q].name), "%s", names[q]);
+        out[q].launches = (int64_t)steps;
+        out[q].total_ms = tot[q];
+        out[q].bytes_per_launch = bytes[q];
+        ++*n;
+    }
+    g->ev_used = 0;
+    return FMX_OK;
+}
+
+void fmx_destroy(fmx_grid *g) {
+    if (!g) return;
+    for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
+    delete g;
+}
 
 const char *fmx_strerror(fmx_status s) {
     switch (s) {

@@ -42,7 +42,8 @@ Fused2dShape fused2d_shape(const Geo &g, int m, int passes);
 // n_x (column pairs never straddle the periodic seam).  Returns the number
 // of kernels launched or -1.
 bool fused2d_pol_supported(const Geo &g);
-int launch_fused2d_pol(const Geo &g, const Coef<float> &c, const Fused2dArgs<float> &a, cudaStream_t s);
+int launch_fused2d_pol(const Geo &g, const Coef<float> &c, const Fused2dArgs<float> &a, cudaStream_t s,
+                       cudaEvent_t *ev = nullptr);
 Fused2dShape fused2d_pol_shape(const Geo &g, int m, int passes);
 
 }  // namespace fmx

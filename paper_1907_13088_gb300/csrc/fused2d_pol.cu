@@ -479,14 +479,20 @@ struct PolLauncher {
     }
 };
 
+// events (optional): ev[0] before the TE launch, ev[1] between, ev[2] after TM
+thread_local cudaEvent_t *t_ev = nullptr;
+
 template <int M, int P, bool HJ>
 int run_both(const Geo &g, const Coef2 &c, const Fused2dArgs<float> &a, cudaStream_t s, Fused2dShape *sh) {
     if (sh) {
         *sh = PolLauncher<TE, M, P, HJ>::shape(g);
         return 0;
     }
+    if (t_ev) cudaEventRecord(t_ev[0], s);
     PolLauncher<TE, M, P, HJ>::run(g, c, a, s);
+    if (t_ev) cudaEventRecord(t_ev[1], s);
     PolLauncher<TM, M, P, HJ>::run(g, c, a, s);
+    if (t_ev) cudaEventRecord(t_ev[2], s);
     return 2;
 }
 
@@ -536,10 +542,14 @@ Coef2 make_coef2(const Coef<float> &c, int passes) {
 
 bool fused2d_pol_supported(const Geo &g) { return g.nx % 2 == 0; }
 
-int launch_fused2d_pol(const Geo &g, const Coef<float> &c, const Fused2dArgs<float> &a, cudaStream_t s) {
+int launch_fused2d_pol(const Geo &g, const Coef<float> &c, const Fused2dArgs<float> &a, cudaStream_t s,
+                       cudaEvent_t *ev) {
     const bool hj = a.J[0] != nullptr;
     const int p = hj ? a.passes : 0;
-    return pol_dispatch(g, make_coef2(c, p), a, s, a.m, hj, p, nullptr);
+    t_ev = ev;
+    const int n = pol_dispatch(g, make_coef2(c, p), a, s, a.m, hj, p, nullptr);
+    t_ev = nullptr;
+    return n;
 }
 
 Fused2dShape fused2d_pol_shape(const Geo &g, int m, int passes) {

@@ -46,6 +46,11 @@ class fmx_buffers(ctypes.Structure):
                 ("work", ctypes.c_void_p), ("work_bytes", ctypes.c_size_t)]
 
 
+class fmx_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("bytes_per_launch", ctypes.c_double)]
+
+
 class fmx_diag(ctypes.Structure):
     _fields_ = [("w_scheme", ctypes.c_double), ("w_plain", ctypes.c_double), ("divb_max", ctypes.c_double),
                 ("divb_l2", ctypes.c_double), ("gauss_max", ctypes.c_double), ("gauss_l2", ctypes.c_double),
@@ -80,6 +85,9 @@ def _load():
         "fmx_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "fmx_last_error": (ctypes.c_char_p, []),
         "fmx_step_static": (ctypes.c_int, [P, vpp, vpp, vpp, ctypes.c_int]),
+        "fmx_profile_enable": (ctypes.c_int, [G, ctypes.c_int]),
+        "fmx_profile_read": (ctypes.c_int, [G, ctypes.POINTER(fmx_kernel_stat), ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_int)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -109,6 +117,8 @@ fmx_destroy = _lib.fmx_destroy
 fmx_strerror = _lib.fmx_strerror
 fmx_last_error = _lib.fmx_last_error
 fmx_step_static = _lib.fmx_step_static
+fmx_profile_enable = _lib.fmx_profile_enable
+fmx_profile_read = _lib.fmx_profile_read
 FMX_STATIC_SCRATCH_BYTES = 4 << 20
 
 
@@ -284,6 +294,16 @@ class Grid:
         out = (ctypes.c_double * FMX_NCOEF)()
         check(fmx_coefficients(self.handle, out, FMX_NCOEF), "fmx_coefficients")
         return np.array(out[:])
+
+    def profile(self, enable: bool):
+        check(fmx_profile_enable(self.handle, int(bool(enable))), "fmx_profile_enable")
+
+    def profile_read(self) -> list:
+        arr = (fmx_kernel_stat * 4)()
+        n = ctypes.c_int(0)
+        check(fmx_profile_read(self.handle, arr, 4, ctypes.byref(n)), "fmx_profile_read")
+        return [{"name": arr[i].name.decode(), "launches": arr[i].launches, "total_ms": arr[i].total_ms,
+                 "bytes_per_launch": arr[i].bytes_per_launch} for i in range(n.value)]
 
     @property
     def dt(self) -> float:
