@@ -217,6 +217,60 @@ void *fmx_field_ptr(const fmx_grid *g, int c);
 /* Number of device kernels this grid has launched since fmx_bind. */
 int64_t fmx_launch_count(const fmx_grid *g);
 
+/* ---- Batched step (many independent 2D grids, one launch per step) ----
+ * The grids of a batch are advanced together: every step is ONE persistent
+ * kernel launch whose CTAs loop over (grid, strip, row-segment) tiles of all
+ * grids, longest tiles first; the launches of fmx_batch_step are replayed
+ * from CUDA graphs (two steps per graph) captured on first use.  Each grid
+ * has its own sizes, cell sizes, dt / Courant number and buffers; all share
+ * the precision (FP32), m, the current-filter passes, and the stream, which
+ * must not be the legacy default stream (graph capture needs a stream of its
+ * own).  Every grid uses the single-column fused tile of the 2D engine, so
+ * odd n_x are fine.  The same equations as fmx_step (Secs. 2.2.1-2.2.2). */
+typedef struct fmx_batch fmx_batch;
+
+/* Validates each of the n parameter sets (2D, FP32, fixed m, equal m,
+ * filter passes and target across the batch, stream not NULL) and creates
+ * the batch handle (host memory only).  Errors: FMX_EINVAL, FMX_ECFL,
+ * FMX_EUNSUPPORTED (an (m, passes) pair without a batched kernel). */
+fmx_status fmx_batch_create(const fmx_params *ps, int n, fmx_batch **out);
+
+/* Device bytes the batch needs for its tile descriptors and work list. */
+size_t fmx_batch_workspace_bytes(const fmx_batch *b);
+
+/* Lends the batch the buffers of its n grids (bufs[i] as in fmx_bind, set 0
+ * and set 1 required, J all NULL or all set in every grid) and a
+ * 256-byte-aligned workspace; builds the work list with the automatic tile
+ * rows.  Errors: FMX_EINVAL, FMX_ECUDA. */
+fmx_status fmx_batch_bind(fmx_batch *b, const fmx_buffers *bufs, void *work, size_t work_bytes);
+
+/* Copy grid i's components in or out of its current state set (as
+ * fmx_set_fields / fmx_get_fields; get synchronises). */
+fmx_status fmx_batch_set_fields(fmx_batch *b, int i, unsigned mask, const void *const *src, int where);
+fmx_status fmx_batch_get_fields(fmx_batch *b, int i, unsigned mask, void *const *dst, int where);
+
+/* Rows per tile segment: rows > 0 caps every grid's segment at that many
+ * rows; 0 selects the automatic choice.  Rebuilds the work list and drops
+ * the captured graphs.  The tile's row extent changes only which rows are
+ * recomputed as warm-up, never a result. */
+fmx_status fmx_batch_set_rows(fmx_batch *b, int rows);
+
+/* Autotuner: times each candidate row extent (automatic, 1024, 512, 256, 128,
+ * 64, 32) over `trial_steps` graph-replayed steps with CUDA events, keeps
+ * the fastest and returns it in *chosen (0 = automatic).  The trial steps
+ * advance the grids' state: set the fields afterwards. */
+fmx_status fmx_batch_tune(fmx_batch *b, int trial_steps, int *chosen);
+
+/* Enqueues nsteps steps of every grid (graph replays plus at most one
+ * plain launch).  Asynchronous.  Errors: FMX_ESTATE, FMX_EINVAL, FMX_ECUDA. */
+fmx_status fmx_batch_step(fmx_batch *b, int nsteps);
+
+/* Work items (tiles) of the current work list, and kernels launched. */
+int fmx_batch_items(const fmx_batch *b);
+int64_t fmx_batch_launch_count(const fmx_batch *b);
+
+void fmx_batch_destroy(fmx_batch *b);
+
 /* Per-kernel timing of the fused engine: while enabled, every kernel of
  * fmx_step is bracketed by CUDA events recorded on the grid's stream.
  * fmx_profile_read synchronises, returns one record per kernel kind (the

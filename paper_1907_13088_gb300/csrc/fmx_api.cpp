@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <new>
+#include <algorithm>
 #include <vector>
 
 #include "fmx.h"
@@ -779,3 +780,342 @@ fmx_status staged_steps_on(const fmx_params *p, void *const E[3], void *const B[
 }
 
 }  // namespace fmx
+
+// ---------------------------------------------------------------------------
+// Batched step
+// ---------------------------------------------------------------------------
+
+struct fmx_batch {
+    int n = 0;
+    std::vector<fmx_params> p;
+    std::vector<fmx::BatchGrid> grids;  // host copy of the descriptors
+    int m = 0, passes = 0;
+    bool hj = false;
+    cudaStream_t stream = nullptr;
+    int threads = 0, halo = 0, width = 0, bps = 1, sms = 1;
+    size_t smem = 0;
+    bool bound = false;
+    fmx::BatchGrid *d_grids = nullptr;
+    fmx::BatchItem *d_items = nullptr;
+    size_t max_items = 0;
+    int nitems = 0;
+    int rows_policy = 0;
+    int parity = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t launches = 0, steps = 0;
+};
+
+namespace {
+
+void batch_drop_graphs(fmx_batch *b) {
+    for (int q = 0; q < 2; ++q)
+        if (b->graph[q]) {
+            cudaGraphExecDestroy(b->graph[q]);
+            b->graph[q] = nullptr;
+        }
+}
+
+// Rows per segment of grid i under the current policy.  The automatic choice
+// aims at about four tiles per resident CTA slot over the whole batch.
+int batch_rows(const fmx_batch *b, int i) {
+    const int ny = (int)b->p[i].n[1];
+    if (b->rows_policy > 0) return b->rows_policy < ny ? b->rows_policy : ny;
+    double work = 0.0;  // total (strips x rows) of the batch
+    for (int k = 0; k < b->n; ++k) {
+        const int ns = ((int)b->p[k].n[0] + b->width - 1) / b->width;
+        work += (double)ns * b->p[k].n[1];
+    }
+    const double target = 4.0 * b->bps * b->sms;
+    int L = (int)(work / target) + 1;
+    if (L < 32) L = 32;
+    return L < ny ? L : ny;
+}
+
+fmx_status batch_build(fmx_batch *b) {
+    std::vector<fmx::BatchItem> items;
+    std::vector<double> cost;
+    const int warm = 3 * b->m + 2 * b->passes + 8;
+    for (int i = 0; i < b->n; ++i) {
+        fmx::BatchGrid &G = b->grids[i];
+        G.L = batch_rows(b, i);
+        G.W = b->width;
+        G.nstrip = (G.g.nx + G.W - 1) / G.W;
+        const int nseg = (G.g.ny + G.L - 1) / G.L;
+        for (int st = 0; st < G.nstrip; ++st)
+            for (int sg = 0; sg < nseg; ++sg) {
+                items.push_back({i, st, sg});
+                const int rows = (sg + 1) * G.L <= G.g.ny ? G.L : G.g.ny - sg * G.L;
+                cost.push_back((double)rows + warm);
+            }
+    }
+    if (items.size() > b->max_items) return fail(FMX_EINVAL, "batch work list larger than its workspace");
+    // longest tiles first
+    std::vector<size_t> order(items.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+    std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+    std::vector<fmx::BatchItem> sorted(items.size());
+    for (size_t k = 0; k < order.size(); ++k) sorted[k] = items[order[k]];
+    b->nitems = (int)sorted.size();
+    cudaError_t e = cudaMemcpyAsync(b->d_grids, b->grids.data(), sizeof(fmx::BatchGrid) * b->n,
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_items, sorted.data(), sizeof(fmx::BatchItem) * sorted.size(), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch descriptor upload");
+    batch_drop_graphs(b);
+    return FMX_OK;
+}
+
+int batch_blocks(const fmx_batch *b) {
+    const int slots = b->bps * b->sms;
+    return b->nitems < slots ? b->nitems : slots;
+}
+
+fmx_status batch_launch(fmx_batch *b, int parity) {
+    int nl = fmx::launch_fused2d_batch(b->m, b->passes, b->hj, b->d_grids, b->d_items, b->nitems, parity,
+                                       batch_blocks(b), b->smem, b->stream);
+    if (nl < 0) return fail(FMX_EUNSUPPORTED, "batched kernel not instantiated");
+    b->launches += nl;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "batched kernel launch");
+    return FMX_OK;
+}
+
+// graph of two steps starting from `parity` (captured once per parity)
+fmx_status batch_graph(fmx_batch *b, int parity, cudaGraphExec_t *out) {
+    if (b->graph[parity]) {
+        *out = b->graph[parity];
+        return FMX_OK;
+    }
+    cudaGraph_t gr = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    const int64_t l0 = b->launches;
+    fmx_status s1 = batch_launch(b, parity);
+    fmx_status s2 = s1 == FMX_OK ? batch_launch(b, 1 - parity) : s1;
+    b->launches = l0;  // captured, not run
+    e = cudaStreamEndCapture(b->stream, &gr);
+    if (s2 != FMX_OK) {
+        if (gr) cudaGraphDestroy(gr);
+        return s2;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&b->graph[parity], gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    *out = b->graph[parity];
+    return FMX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fmx_status fmx_batch_create(const fmx_params *ps, int n, fmx_batch **out) {
+    if (!ps || !out || n < 1) return fail(FMX_EINVAL, "bad arguments");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        const fmx_params &q = ps[i];
+        if (q.dims != 2 || q.precision != FMX_F32 || q.iter_mode != FMX_ITER_FIXED)
+            return fail(FMX_EINVAL, "grid %d: the batch takes 2D FP32 grids with fixed m", i);
+        if (q.filter_target == FMX_FILTER_FIELDS && q.filter_passes > 0)
+            return fail(FMX_EINVAL, "grid %d: field filtering is not part of the batched step", i);
+        if (q.m != ps[0].m || q.filter_passes != ps[0].filter_passes || q.filter_target != ps[0].filter_target ||
+            q.stream != ps[0].stream)
+            return fail(FMX_EINVAL, "grid %d: m, filter and stream must match across the batch", i);
+    }
+    if (!ps[0].stream) return fail(FMX_EINVAL, "the batch needs a stream other than the legacy default stream");
+    fmx_batch *b = new (std::nothrow) fmx_batch;
+    if (!b) return fail(FMX_EINVAL, "out of host memory");
+    b->n = n;
+    b->p.assign(ps, ps + n);
+    b->grids.resize(n);
+    b->m = ps[0].m;
+    b->passes = ps[0].filter_target == FMX_FILTER_CURRENT ? ps[0].filter_passes : 0;
+    b->stream = (cudaStream_t)ps[0].stream;
+    for (int i = 0; i < n; ++i) {
+        fmx_params q = ps[i];
+        q.engine = FMX_ENGINE_STAGED;
+        double dt = 0.0;
+        fmx_status s = validate(&q, &dt, nullptr);
+        if (s != FMX_OK) {
+            delete b;
+            return s;
+        }
+        double co[FMX_NCOEF];
+        coefficients(&q, dt, co);
+        memset(&b->grids[i], 0, sizeof(fmx::BatchGrid));
+        b->grids[i].g = geo_of(&q);
+        b->grids[i].c = make_coef<float>(co);
+    }
+    // geometry with and without a current (bind decides)
+    if (fmx::fused2d_batch_geometry(b->m, 0, false, &b->threads, &b->halo, &b->width, &b->smem, &b->bps) != 0) {
+        delete b;
+        return fail(FMX_EUNSUPPORTED, "no batched kernel for m = %d", ps[0].m);
+    }
+    *out = b;
+    return FMX_OK;
+}
+
+size_t fmx_batch_workspace_bytes(const fmx_batch *b) {
+    if (!b) return 0;
+    // work list bound: the smallest row extent the tuner tries (32 rows)
+    size_t items = 0;
+    const int width = b->width > 0 ? b->width : 1;
+    for (int i = 0; i < b->n; ++i) {
+        const size_t ns = ((size_t)b->p[i].n[0] + width - 1) / width;
+        items += ns * (((size_t)b->p[i].n[1] + 31) / 32 + 1);
+    }
+    return align_up(sizeof(fmx::BatchGrid) * b->n, kAlign) + align_up(sizeof(fmx::BatchItem) * items, kAlign);
+}
+
+fmx_status fmx_batch_bind(fmx_batch *b, const fmx_buffers *bufs, void *work, size_t work_bytes) {
+    if (!b || !bufs || !work) return fail(FMX_EINVAL, "NULL argument");
+    if ((uintptr_t)work % kAlign) return fail(FMX_EINVAL, "workspace must be 256-byte aligned");
+    const size_t need = fmx_batch_workspace_bytes(b);
+    if (work_bytes < need) return fail(FMX_EINVAL, "batch workspace of %zu bytes needed", need);
+    const bool hj = bufs[0].J[0] != nullptr;
+    for (int i = 0; i < b->n; ++i) {
+        fmx::BatchGrid &G = b->grids[i];
+        for (int s = 0; s < 2; ++s)
+            for (int c = 0; c < 3; ++c) {
+                if (!bufs[i].E[s][c] || !bufs[i].B[s][c]) return fail(FMX_EINVAL, "grid %d: NULL field buffer", i);
+                if (((uintptr_t)bufs[i].E[s][c] | (uintptr_t)bufs[i].B[s][c]) % 16)
+                    return fail(FMX_EINVAL, "grid %d: field buffers must be 16-byte aligned", i);
+                G.E[s][c] = (const float *)bufs[i].E[s][c];
+                G.B[s][c] = (const float *)bufs[i].B[s][c];
+            }
+        for (int c = 0; c < 3; ++c) {
+            if ((bufs[i].J[c] != nullptr) != hj) return fail(FMX_EINVAL, "grid %d: J buffers all set or all NULL", i);
+            G.J[c] = (const float *)bufs[i].J[c];
+        }
+    }
+    b->hj = hj && b->passes >= 0;
+    if (fmx::fused2d_batch_geometry(b->m, b->hj ? b->passes : 0, b->hj, &b->threads, &b->halo, &b->width, &b->smem,
+                                    &b->bps) != 0)
+        return fail(FMX_EUNSUPPORTED, "no batched kernel for m = %d, passes = %d", b->m, b->passes);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) b->sms = 1;
+    char *w = (char *)work;
+    b->d_grids = (fmx::BatchGrid *)w;
+    w += align_up(sizeof(fmx::BatchGrid) * b->n, kAlign);
+    b->d_items = (fmx::BatchItem *)w;
+    b->max_items = (work_bytes - align_up(sizeof(fmx::BatchGrid) * b->n, kAlign)) / sizeof(fmx::BatchItem);
+    b->parity = 0;
+    b->launches = b->steps = 0;
+    b->bound = true;
+    return batch_build(b);
+}
+
+fmx_status fmx_batch_set_fields(fmx_batch *b, int i, unsigned mask, const void *const *src, int where) {
+    if (!b || !src || i < 0 || i >= b->n) return fail(FMX_EINVAL, "bad arguments");
+    if (!b->bound) return fail(FMX_ESTATE, "batch not bound");
+    if (mask & ~(unsigned)(FMX_E | FMX_B)) return fail(FMX_EINVAL, "mask holds bits other than E and B");
+    const fmx::BatchGrid &G = b->grids[i];
+    const size_t sp = (size_t)G.g.nx * 4, dp = (size_t)G.g.pitch * 4;
+    for (int c = 0; c < 6; ++c) {
+        if (!(mask & (1u << c))) continue;
+        void *dst = (void *)(c < 3 ? G.E[b->parity][c] : G.B[b->parity][c - 3]);
+        cudaError_t e = cudaMemcpy2DAsync(dst, dp, src[c], sp, sp, (size_t)G.g.ny, cudaMemcpyDefault, b->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2DAsync");
+    }
+    if (where == FMX_HOST) {
+        cudaError_t e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    }
+    return FMX_OK;
+}
+
+fmx_status fmx_batch_get_fields(fmx_batch *b, int i, unsigned mask, void *const *dst, int where) {
+    if (!b || !dst || i < 0 || i >= b->n) return fail(FMX_EINVAL, "bad arguments");
+    if (!b->bound) return fail(FMX_ESTATE, "batch not bound");
+    (void)where;
+    const fmx::BatchGrid &G = b->grids[i];
+    const size_t dpch = (size_t)G.g.nx * 4, sp = (size_t)G.g.pitch * 4;
+    for (int c = 0; c < 6; ++c) {
+        if (!(mask & (1u << c))) continue;
+        const void *src = c < 3 ? G.E[b->parity][c] : G.B[b->parity][c - 3];
+        cudaError_t e = cudaMemcpy2DAsync(dst[c], dpch, src, sp, dpch, (size_t)G.g.ny, cudaMemcpyDefault, b->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2DAsync");
+    }
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return FMX_OK;
+}
+
+fmx_status fmx_batch_set_rows(fmx_batch *b, int rows) {
+    if (!b || rows < 0) return fail(FMX_EINVAL, "bad arguments");
+    if (!b->bound) return fail(FMX_ESTATE, "batch not bound");
+    b->rows_policy = rows;
+    return batch_build(b);
+}
+
+fmx_status fmx_batch_step(fmx_batch *b, int nsteps) {
+    if (!b) return fail(FMX_EINVAL, "NULL batch");
+    if (!b->bound) return fail(FMX_ESTATE, "batch not bound");
+    if (nsteps < 0) return fail(FMX_EINVAL, "nsteps < 0");
+    int left = nsteps;
+    if (left % 2) {
+        fmx_status s = batch_launch(b, b->parity);
+        if (s != FMX_OK) return s;
+        b->parity = 1 - b->parity;
+        --left;
+    }
+    if (left > 0) {
+        cudaGraphExec_t ge = nullptr;
+        fmx_status s = batch_graph(b, b->parity, &ge);
+        if (s != FMX_OK) return s;
+        for (int k = 0; k < left / 2; ++k) {
+            cudaError_t e = cudaGraphLaunch(ge, b->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+        }
+        b->launches += left;
+    }
+    b->steps += nsteps;
+    return FMX_OK;
+}
+
+fmx_status fmx_batch_tune(fmx_batch *b, int trial_steps, int *chosen) {
+    if (!b || trial_steps < 2) return fail(FMX_EINVAL, "bad arguments");
+    if (!b->bound) return fail(FMX_ESTATE, "batch not bound");
+    const int cand[] = {0, 1024, 512, 256, 128, 64, 32};
+    float best = 1e30f;
+    int best_rows = 0;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(FMX_ECUDA, "cudaEventCreate");
+    fmx_status s = FMX_OK;
+    for (int rows : cand) {
+        if ((s = fmx_batch_set_rows(b, rows)) != FMX_OK) break;
+        if ((s = fmx_batch_step(b, 2)) != FMX_OK) break;  // capture + warm
+        cudaEventRecord(e0, b->stream);
+        if ((s = fmx_batch_step(b, trial_steps / 2 * 2)) != FMX_OK) break;
+        cudaEventRecord(e1, b->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_rows = rows;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != FMX_OK) return s;
+    if (chosen) *chosen = best_rows;
+    return fmx_batch_set_rows(b, best_rows);
+}
+
+int fmx_batch_items(const fmx_batch *b) { return b ? b->nitems : 0; }
+
+int64_t fmx_batch_launch_count(const fmx_batch *b) { return b ? b->launches : 0; }
+
+void fmx_batch_destroy(fmx_batch *b) {
+    if (!b) return;
+    batch_drop_graphs(b);
+    delete b;
+}
+
+}  // extern "C"

@@ -68,9 +68,12 @@ __device__ __forceinline__ int ring(int r) {
     return q < 0 ? q + D : q;
 }
 
+// One tile: columns [strip W, strip W + W) and rows [seg L, seg L + L) of the
+// output, with the x-halo and warm-up rows recomputed.  Ends after a barrier,
+// so a persistent caller may start another tile right away.
 template <typename T, int M, int P, bool HJ, int NT>
-__global__ void __launch_bounds__(NT, 2)
-    k_fused2d(Fused2dArgs<T> a, Geo g, Coef<T> c, int W, int L, int nstrip) {
+__device__ __forceinline__ void fused2d_tile(const Fused2dArgs<T> &a, const Geo &g, const Coef<T> &c, int W, int L,
+                                             int strip, int seg) {
     using G = Geom<M, P, HJ>;
     constexpr int PX = G::PX, H = G::H, D0 = G::D0, NS = G::NS, TJ = G::TJ;
     constexpr int RW = NT + 2 * PX;
@@ -88,7 +91,6 @@ __global__ void __launch_bounds__(NT, 2)
     const int tid = threadIdx.x;
     for (int q = tid; q < total; q += NT) sm[q] = T(0);
 
-    const int strip = blockIdx.x % nstrip, seg = blockIdx.x / nstrip;
     const int x0 = strip * W;
     const int y0 = seg * L;
     const int y1 = min(y0 + L, g.ny);
@@ -372,6 +374,34 @@ __global__ void __launch_bounds__(NT, 2)
     }
 }
 
+template <typename T, int M, int P, bool HJ, int NT>
+__global__ void __launch_bounds__(NT, 2)
+    k_fused2d(Fused2dArgs<T> a, Geo g, Coef<T> c, int W, int L, int nstrip) {
+    fused2d_tile<T, M, P, HJ, NT>(a, g, c, W, L, blockIdx.x % nstrip, blockIdx.x / nstrip);
+}
+
+// Batched step: a persistent grid-stride loop over (grid, strip, segment)
+// tiles of many independent grids (longest tiles first), one launch per step.
+template <int M, int P, bool HJ, int NT>
+__global__ void __launch_bounds__(NT, 2)
+    k_fused2d_batch(const BatchGrid *__restrict__ grids, const BatchItem *__restrict__ items, int nitems, int parity) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BatchItem w = items[it];
+        const BatchGrid &G = grids[w.grid];
+        Fused2dArgs<float> a;
+        for (int q = 0; q < 3; ++q) {
+            a.E[q] = G.E[parity][q];
+            a.B[q] = G.B[parity][q];
+            a.J[q] = HJ ? G.J[q] : nullptr;
+            a.Eo[q] = const_cast<float *>(G.E[1 - parity][q]);
+            a.Bo[q] = const_cast<float *>(G.B[1 - parity][q]);
+        }
+        a.m = M;
+        a.passes = P;
+        fused2d_tile<float, M, P, HJ, NT>(a, G.g, G.c, G.W, G.L, w.strip, w.seg);
+    }
+}
+
 template <typename T, int M, int P, bool HJ>
 struct Launcher {
     static constexpr int NT = Cfg<T>::NT;
@@ -470,6 +500,41 @@ Fused2dShape fused2d_shape(const Geo &g, int m, int passes) {
     Coef<T> c{};
     dispatch<T>(g, c, a, nullptr, m, passes >= 0, passes >= 0 ? passes : 0, &sh);
     return sh;
+}
+
+int fused2d_batch_geometry(int m, int passes, bool hj, int *threads, int *halo, int *width, size_t *smem,
+                           int *blocks_per_sm) {
+    int rc = -1;
+#define FMX_BG(MM, PP, HH)                                                                                   \
+    if (m == MM && passes == PP && hj == HH) {                                                              \
+        using Gm = Geom<MM, PP, HH>;                                                                       \
+        constexpr int NT = Cfg<float>::NT;                                                                 \
+        *threads = NT;                                                                                     \
+        *halo = Gm::H;                                                                                     \
+        *width = NT - 2 * Gm::H - 1;                                                                       \
+        *smem = smem_elems<float, MM, PP, HH, NT>() * sizeof(float);                                       \
+        auto k = k_fused2d_batch<MM, PP, HH, NT>;                                                          \
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);                  \
+        int nb = 0;                                                                                        \
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NT, *smem) != cudaSuccess || nb < 1) nb = 1; \
+        *blocks_per_sm = nb;                                                                               \
+        rc = 0;                                                                                            \
+    }
+    FMX_BG(4, 0, false) FMX_BG(4, 3, true) FMX_BG(2, 0, false) FMX_BG(1, 0, false) FMX_BG(0, 0, false)
+#undef FMX_BG
+    return rc;
+}
+
+int launch_fused2d_batch(int m, int passes, bool hj, const BatchGrid *grids, const BatchItem *items, int nitems,
+                         int parity, int nblocks, size_t smem, cudaStream_t s) {
+#define FMX_BL(MM, PP, HH)                                                                       \
+    if (m == MM && passes == PP && hj == HH) {                                                  \
+        k_fused2d_batch<MM, PP, HH, Cfg<float>::NT><<<nblocks, Cfg<float>::NT, smem, s>>>(grids, items, nitems, parity); \
+        return 1;                                                                              \
+    }
+    FMX_BL(4, 0, false) FMX_BL(4, 3, true) FMX_BL(2, 0, false) FMX_BL(1, 0, false) FMX_BL(0, 0, false)
+#undef FMX_BL
+    return -1;
 }
 
 template int launch_fused2d<float>(const Geo &, const Coef<float> &, const Fused2dArgs<float> &, cudaStream_t);

@@ -46,4 +46,24 @@ int launch_fused2d_pol(const Geo &g, const Coef<float> &c, const Fused2dArgs<flo
                        cudaEvent_t *ev = nullptr);
 Fused2dShape fused2d_pol_shape(const Geo &g, int m, int passes);
 
+// Batched step (fused2d.cu): independent FP32 grids advanced by one
+// persistent launch per step over (grid, strip, segment) tiles.
+struct BatchGrid {
+    Geo g;
+    Coef<float> c;
+    const float *E[2][3];  // state sets; a step reads set `parity`, writes 1 - parity
+    const float *B[2][3];
+    const float *J[3];
+    int W, L, nstrip;      // tile width (columns written), rows per segment, strips
+};
+struct BatchItem {
+    int grid, strip, seg;
+};
+// Tile geometry and occupancy of the batched kernel for (m, passes, current);
+// returns -1 when that combination is not instantiated.
+int fused2d_batch_geometry(int m, int passes, bool hj, int *threads, int *halo, int *width, size_t *smem,
+                           int *blocks_per_sm);
+int launch_fused2d_batch(int m, int passes, bool hj, const BatchGrid *grids, const BatchItem *items, int nitems,
+                         int parity, int nblocks, size_t smem, cudaStream_t s);
+
 }  // namespace fmx

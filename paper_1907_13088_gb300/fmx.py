@@ -86,6 +86,17 @@ def _load():
         "fmx_last_error": (ctypes.c_char_p, []),
         "fmx_step_static": (ctypes.c_int, [P, vpp, vpp, vpp, ctypes.c_int]),
         "fmx_profile_enable": (ctypes.c_int, [G, ctypes.c_int]),
+        "fmx_batch_create": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(G)]),
+        "fmx_batch_workspace_bytes": (ctypes.c_size_t, [G]),
+        "fmx_batch_bind": (ctypes.c_int, [G, ctypes.POINTER(fmx_buffers), ctypes.c_void_p, ctypes.c_size_t]),
+        "fmx_batch_set_fields": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_uint, vpp, ctypes.c_int]),
+        "fmx_batch_get_fields": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_uint, vpp, ctypes.c_int]),
+        "fmx_batch_set_rows": (ctypes.c_int, [G, ctypes.c_int]),
+        "fmx_batch_tune": (ctypes.c_int, [G, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+        "fmx_batch_step": (ctypes.c_int, [G, ctypes.c_int]),
+        "fmx_batch_items": (ctypes.c_int, [G]),
+        "fmx_batch_launch_count": (ctypes.c_int64, [G]),
+        "fmx_batch_destroy": (None, [G]),
         "fmx_profile_read": (ctypes.c_int, [G, ctypes.POINTER(fmx_kernel_stat), ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_int)]),
     }
@@ -118,6 +129,17 @@ fmx_strerror = _lib.fmx_strerror
 fmx_last_error = _lib.fmx_last_error
 fmx_step_static = _lib.fmx_step_static
 fmx_profile_enable = _lib.fmx_profile_enable
+fmx_batch_create = _lib.fmx_batch_create
+fmx_batch_workspace_bytes = _lib.fmx_batch_workspace_bytes
+fmx_batch_bind = _lib.fmx_batch_bind
+fmx_batch_set_fields = _lib.fmx_batch_set_fields
+fmx_batch_get_fields = _lib.fmx_batch_get_fields
+fmx_batch_set_rows = _lib.fmx_batch_set_rows
+fmx_batch_tune = _lib.fmx_batch_tune
+fmx_batch_step = _lib.fmx_batch_step
+fmx_batch_items = _lib.fmx_batch_items
+fmx_batch_launch_count = _lib.fmx_batch_launch_count
+fmx_batch_destroy = _lib.fmx_batch_destroy
 fmx_profile_read = _lib.fmx_profile_read
 FMX_STATIC_SCRATCH_BYTES = 4 << 20
 
@@ -347,3 +369,109 @@ def create_status(params: fmx_params):
     if s == FMX_OK:
         fmx_destroy(h)
     return s, w.value
+
+
+class Batch:
+    """Many independent 2D FP32 grids advanced together (fmx_batch_*): one
+    persistent launch per step, replayed from captured CUDA graphs.  Device
+    buffers are PyTorch tensors; the batch runs on a stream of its own."""
+
+    def __init__(self, shapes, courants, m=4, filter_passes=0, with_current=False, device="cuda", d=(1.0, 1.0)):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        self.stream = torch.cuda.Stream(self.device)
+        self.n = len(shapes)
+        self.shapes = [tuple(int(v) for v in sh) for sh in shapes]
+        params = (fmx_params * self.n)()
+        for i, (sh, cf) in enumerate(zip(self.shapes, courants)):
+            params[i] = make_params(sh, d=tuple(d) + (1.0,), courant=float(cf), precision=FMX_F32, m=m,
+                                    filter_passes=filter_passes,
+                                    filter_target=FMX_FILTER_CURRENT if with_current else FMX_FILTER_NONE,
+                                    stream=ctypes.c_void_p(self.stream.cuda_stream))
+        self.params = params
+        h = ctypes.c_void_p()
+        check(fmx_batch_create(params, self.n, ctypes.byref(h)), "fmx_batch_create")
+        self.handle = h
+        # one slab: per grid 12 state arrays (+3 current), each at a 256-byte boundary
+        self.pitch = [(sh[0] + 3) // 4 * 4 for sh in self.shapes]
+        sizes = [(p * sh[1] + 63) // 64 * 64 for p, sh in zip(self.pitch, self.shapes)]
+        ncomp = 12 + (3 if with_current else 0)
+        offs, tot = [], 0
+        for sz in sizes:
+            offs.append(tot)
+            tot += ncomp * sz
+        self._slab = torch.zeros(tot, dtype=torch.float32, device=self.device)
+        base = self._slab.data_ptr()
+        bufs = (fmx_buffers * self.n)()
+        for i in range(self.n):
+            ptr = lambda k: base + 4 * (offs[i] + k * sizes[i])
+            for s_ in range(2):
+                for c in range(3):
+                    bufs[i].E[s_][c] = ptr(s_ * 6 + c)
+                    bufs[i].B[s_][c] = ptr(s_ * 6 + 3 + c)
+            for c in range(3):
+                bufs[i].J[c] = ptr(12 + c) if with_current else None
+        self._offs, self._sizes = offs, sizes
+        wb = fmx_batch_workspace_bytes(self.handle)
+        self._work = torch.zeros(wb + 256, dtype=torch.uint8, device=self.device)
+        wbase = (self._work.data_ptr() + 255) // 256 * 256
+        self.bufs = bufs
+        torch.cuda.synchronize()
+        check(fmx_batch_bind(self.handle, bufs, wbase, wb), "fmx_batch_bind")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fmx_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_fields(self, i, E, B):
+        keep = [np.ascontiguousarray(F[c], dtype=np.float32) for F in (E, B) for c in range(3)]
+        ptrs = (ctypes.c_void_p * 6)(*[k.ctypes.data for k in keep])
+        check(fmx_batch_set_fields(self.handle, i, FMX_E | FMX_B, ptrs, FMX_HOST), "fmx_batch_set_fields")
+
+    def set_current(self, i, J):
+        """Writes grid i's current buffers directly (device copy on the batch stream)."""
+        nx, ny = self.shapes[i]
+        with self.torch.cuda.stream(self.stream):
+            for c in range(3):
+                o = self._offs[i] + (12 + c) * self._sizes[i]
+                view = self._slab[o:o + self.pitch[i] * ny].view(ny, self.pitch[i])
+                view[:, :nx].copy_(self.torch.from_numpy(np.ascontiguousarray(J[c][0], dtype=np.float32)))
+        self.stream.synchronize()
+
+    def get_fields(self, i):
+        nx, ny = self.shapes[i]
+        host = np.zeros((6, 1, ny, nx), dtype=np.float32)
+        ptrs = (ctypes.c_void_p * 6)(*[host[c].ctypes.data for c in range(6)])
+        check(fmx_batch_get_fields(self.handle, i, FMX_E | FMX_B, ptrs, FMX_HOST), "fmx_batch_get_fields")
+        return host[:3], host[3:]
+
+    def set_rows(self, rows):
+        check(fmx_batch_set_rows(self.handle, int(rows)), "fmx_batch_set_rows")
+
+    def tune(self, trial_steps=20) -> int:
+        chosen = ctypes.c_int(0)
+        check(fmx_batch_tune(self.handle, int(trial_steps), ctypes.byref(chosen)), "fmx_batch_tune")
+        return chosen.value
+
+    def step(self, nsteps=1):
+        check(fmx_batch_step(self.handle, int(nsteps)), "fmx_batch_step")
+
+    def sync(self):
+        self.stream.synchronize()
+
+    @property
+    def items(self) -> int:
+        return int(fmx_batch_items(self.handle))
+
+    @property
+    def launches(self) -> int:
+        return int(fmx_batch_launch_count(self.handle))

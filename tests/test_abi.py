@@ -108,3 +108,22 @@ def test_sizes(fmx):
     assert fmx.fmx_workspace_bytes(ctypes.byref(fused)) < 2 * fb
     bad = fmx.make_params((16, 16), courant=2.0)
     assert fmx.fmx_workspace_bytes(ctypes.byref(bad)) == 0
+
+
+def test_batch_validation(fmx):
+    import ctypes
+    stream = ctypes.c_void_p(0x1)  # any non-NULL handle: create does no device work
+    good = [fmx.make_params((64, 40), courant=0.5, stream=stream), fmx.make_params((33, 70), courant=0.9, stream=stream)]
+    arr = (fmx.fmx_params * 2)(*good)
+    h = ctypes.c_void_p()
+    assert fmx.fmx_batch_create(arr, 2, ctypes.byref(h)) == fmx.FMX_OK
+    assert fmx.fmx_batch_workspace_bytes(h) > 0
+    fmx.fmx_batch_destroy(h)
+    bad = [fmx.make_params((64, 40), courant=0.5, stream=stream), fmx.make_params((33, 70), m=3, stream=stream)]
+    assert fmx.fmx_batch_create((fmx.fmx_params * 2)(*bad), 2, ctypes.byref(h)) == fmx.FMX_EINVAL
+    nostream = [fmx.make_params((64, 40), courant=0.5)]
+    assert fmx.fmx_batch_create((fmx.fmx_params * 1)(*nostream), 1, ctypes.byref(h)) == fmx.FMX_EINVAL
+    cfl = [fmx.make_params((64, 40), courant=1.5, stream=stream)]
+    assert fmx.fmx_batch_create((fmx.fmx_params * 1)(*cfl), 1, ctypes.byref(h)) == fmx.FMX_ECFL
+    f64 = [fmx.make_params((64, 40), precision=1, stream=stream)]
+    assert fmx.fmx_batch_create((fmx.fmx_params * 1)(*f64), 1, ctypes.byref(h)) == fmx.FMX_EINVAL
