@@ -77,6 +77,8 @@ def _configure(lib):
     lib.orc_div_b.argtypes = [P, dp, dp]
     lib.orc_gauss_e.argtypes = [P, dp, dp]
     lib.orc_energy.argtypes = [P, dp, dp, dp, dp]
+    lib.orc_adjoint_step.argtypes = [P, dp, dp, dp]
+    lib.orc_adjoint_step.restype = ctypes.c_int
     return lib
 
 
@@ -289,3 +291,16 @@ def energy(p: Params, E, B):
     cp = p._c()
     _load().orc_energy(ctypes.byref(cp), _dp(E), _dp(B), ctypes.byref(ws), ctypes.byref(wp))
     return ws.value, wp.value
+
+
+def adjoint_step(p: Params, Ebar, Bbar):
+    """One adjoint step: returns (dL/dE^n, dL/dB^{n+1/2}, dL/dj) from
+    dL/d(E^{n+1}, B^{n+3/2}).  Fixed m only."""
+    Eb = _field(p, Ebar, "Ebar")
+    Bb = _field(p, Bbar, "Bbar")
+    jb = np.zeros(p.array_shape)
+    cp = p._c()
+    rc = _load().orc_adjoint_step(ctypes.byref(cp), _dp(Eb), _dp(Bb), _dp(jb))
+    if rc != 0:
+        raise ValueError("the oracle adjoint covers fixed m without field filtering")
+    return Eb, Bb, jb

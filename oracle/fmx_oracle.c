@@ -505,3 +505,72 @@ void orc_energy(const orc_params *p, const double *E, const double *B, double *w
     *w_plain = wp * dv / (8.0 * M_PI);
     free(AE); free(Bm); free(SB); free(t);
 }
+
+/* ------------------------------------------------------------------------- */
+/* adjoint of one step (fixed m, current filter or none)                      */
+/* ------------------------------------------------------------------------- */
+
+/* The step is linear in (E^n, B^{n+1/2}, j):
+ *   dE' = C_b S B - q F j,  dE = P dE',  E1 = E + dE,  B1 = B - C_f E1,
+ * with C_f the Faraday curl (forward differences), C_b the source curl
+ * (backward differences), S = diag(alpha_x, alpha_y, alpha_z), F the
+ * binomial filter and P = sum_{s=0}^{m} A^s (Algorithm 1).  A forward
+ * difference transposes to minus the backward one on the periodic lattice,
+ * so C_f^T = C_b; A (Eqs. matrixA_*), S and F are symmetric, hence P too.
+ * Given Ebar, Bbar = dL/d(E1, B1) this returns, in place, dL/d(E, B) and in
+ * jbar the gradient dL/dj:
+ *   u = Ebar - C_b Bbar,  Ebar <- u,  w = P u,
+ *   Bbar <- Bbar + S C_f w,  jbar = -q F w.
+ * Residual mode has no fixed linear map and field filtering is not covered:
+ * both return 1. */
+int orc_adjoint_step(const orc_params *p, double *Ebar, double *Bbar, double *jbar)
+{
+    if (p->residual || (p->filter_target == ORC_FILTER_FIELDS && p->filter_passes > 0)) return 1;
+    shape_t s = shape_of(p);
+    const long n = s.ncell, n3 = 3 * n;
+    double co[ORC_NCOEF];
+    orc_coefficients(p, co);
+    double *u = (double *)malloc(sizeof(double) * n3);
+    double *w = (double *)malloc(sizeof(double) * n3);
+    double *t = (double *)calloc((size_t)n3, sizeof(double));
+    double *tmp = alloc_cells(&s);
+    /* u = Ebar - C_b Bbar: the source curl with alpha -> 1 and no current */
+    {
+        /* C_b Bbar, component by component (the differences of orc_source) */
+        const double *Bx = Bbar, *By = Bbar + n, *Bz = Bbar + 2 * n;
+        double *d = alloc_cells(&s);
+        memset(u, 0, sizeof(double) * n3);
+        dbar(&s, Bz, d, 1, 0); axpy(&s, co[ORC_KY], d, u);
+        dbar(&s, By, d, 2, 0); axpy(&s, -co[ORC_KZ], d, u);
+        dbar(&s, Bx, d, 2, 0); axpy(&s, co[ORC_KZ], d, u + n);
+        dbar(&s, Bz, d, 0, 0); axpy(&s, -co[ORC_KX], d, u + n);
+        dbar(&s, By, d, 0, 0); axpy(&s, co[ORC_KX], d, u + 2 * n);
+        dbar(&s, Bx, d, 1, 0); axpy(&s, -co[ORC_KY], d, u + 2 * n);
+        free(d);
+        for (long c = 0; c < n3; ++c) u[c] = Ebar[c] - u[c];
+    }
+    /* w = P u (Algorithm 1 with u as its right-hand side) */
+    {
+        int sw;
+        double r;
+        orc_solve(p, u, w, &sw, &r);
+    }
+    memcpy(Ebar, u, sizeof(double) * n3);
+    /* Bbar += S C_f w: orc_faraday subtracts C_f w from a zero field */
+    orc_faraday(p, w, t);
+    for (int a = 0; a < 3; ++a) {
+        double *ta = t + a * n;
+        double *sa = (double *)malloc(sizeof(double) * n);
+        alpha(&s, co[ORC_C6], ta, sa, tmp, a);
+        for (long c = 0; c < n; ++c) Bbar[a * n + c] -= sa[c];
+        free(sa);
+    }
+    /* jbar = -q F w */
+    if (jbar) {
+        memcpy(jbar, w, sizeof(double) * n3);
+        if (p->filter_target == ORC_FILTER_CURRENT && p->filter_passes > 0) orc_filter(p, jbar, 3, p->filter_passes);
+        for (long c = 0; c < n3; ++c) jbar[c] *= -co[ORC_Q];
+    }
+    free(u); free(w); free(t); free(tmp);
+    return ORC_OK;
+}

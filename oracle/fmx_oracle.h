@@ -59,6 +59,7 @@ int orc_step(const orc_params *p, double *E, double *B, const double *J, int nst
 void orc_div_b(const orc_params *p, const double *B, double *out);
 void orc_gauss_e(const orc_params *p, const double *E, double *out);
 void orc_energy(const orc_params *p, const double *E, const double *B, double *w_scheme, double *w_plain);
+int orc_adjoint_step(const orc_params *p, double *Ebar, double *Bbar, double *jbar);
 
 #ifdef __cplusplus
 }
