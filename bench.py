@@ -361,6 +361,56 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args):
+    """Differentiable 1024^2 FP32 run: 64 Gaussian-envelope sources
+    (amplitude parameters theta), loss = field energy in the window
+    [448, 576)^2 at the final step, forward + hand-written adjoint with a
+    checkpoint every 50 steps.  Reports forward-only and forward+adjoint
+    cell-updates/s on the same GPU."""
+    import numpy as np
+    import torch
+    from paper_1907_13088_gb300 import build, synth
+    build.build()
+    from paper_1907_13088_gb300 import fmx
+    from paper_1907_13088_gb300.adjoint import GaussSourceRun, make_function
+    shape, N = (1024, 1024), args.steps
+    cxy, phases, theta = synth.gauss_sources(64, shape, seed=1907005)
+    E0, B0, _ = synth.random_fields(shape, seed=1907006)
+    e0 = torch.from_numpy(0.01 * E0[:, 0]).to("cuda", torch.float32)
+    b0 = torch.from_numpy(0.01 * B0[:, 0]).to("cuda", torch.float32)
+    mask = torch.zeros((3, 1024, 1024), device="cuda")
+    mask[:, 448:576, 448:576] = 1.0
+    run = GaussSourceRun(shape, cxy, phases, N, width=8.0, omega0=0.2, m=4, passes=3, courant=0.5,
+                         precision=fmx.FMX_F32, checkpoint_every=50)
+    FieldRun = make_function()
+    th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+    run.forward(theta, e0, b0)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    run.forward(theta, e0, b0)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    EN, BN = FieldRun.apply(th, e0, b0, run, False)
+    loss = 0.5 * ((EN * EN * mask).sum() + (BN * BN * mask).sum())
+    loss.backward()
+    torch.cuda.synchronize()
+    t_both = time.perf_counter() - t0
+    cells = shape[0] * shape[1]
+    line = {
+        "metric": METRIC, "value": round(cells * N / t_both / 1e9, 4), "unit": UNIT, "n_gpus": 1, "steps": N,
+        "warmup": 1, "ms_per_step": round(t_both / N * 1e3, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "differentiable 2D 1024x1024 FP32, 64 Gaussian-envelope sources, loss = window "
+                               "energy [448,576)^2 at the final step, forward + adjoint, checkpoint every 50",
+                   "forward_only_gcells": round(cells * N / t_fwd / 1e9, 4),
+                   "forward_plus_adjoint_gcells": round(cells * N / t_both / 1e9, 4),
+                   "timing": "host wall clock around whole passes, synchronised"},
+        "roofline": None, "gpu_launches": int(run.launches),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def _oracle_sample_rate(n, nsteps, threads):
     """Runs the FP64 oracle on an n x n periodic sample of the workload;
     returns (cell-updates/s, threads used, seconds)."""
@@ -433,7 +483,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
-    ap.add_argument("--workload", choices=("2d4096", "batch256"), default="2d4096")
+    ap.add_argument("--workload", choices=("2d4096", "batch256", "adjoint1024"), default="2d4096")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -441,6 +491,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch256":
         run_batch(args)
+    elif args.workload == "adjoint1024":
+        run_adjoint(args)
     else:
         run_ours(args)
 

@@ -217,6 +217,32 @@ void *fmx_field_ptr(const fmx_grid *g, int c);
 /* Number of device kernels this grid has launched since fmx_bind. */
 int64_t fmx_launch_count(const fmx_grid *g);
 
+/* ---- Adjoint (reverse-mode derivative) of the step ----
+ * The step is linear in (E^n, B^{n+1/2}, j).  fmx_adjoint_step maps
+ * dL/d(E^{n+1}, B^{n+3/2}) (Ebar, Bbar: device arrays in the grid's layout,
+ * updated in place) to dL/d(E^n, B^{n+1/2}) and writes dL/dj^{n+1/2} to
+ * jbar (may be NULL): u = Ebar - C_b Bbar, Ebar <- u, w = sum_{s<=m} A^s u,
+ * Bbar <- Bbar + S C_f w, jbar = -4 pi dt F w, where C_f / C_b are the
+ * Faraday / source curls (Eqs. faraday_x..z, ampere_aux_x..z), S the alpha
+ * averages, F the current filter; it uses C_f^T = C_b and the symmetry of A
+ * (Eqs. matrixA_*), S and F.  Fixed m only; no field filtering.  The work
+ * array (fmx_adjoint_workspace_bytes, 256-byte aligned) is caller-owned.
+ * Errors: FMX_EINVAL, FMX_ESTATE, FMX_EUNSUPPORTED, FMX_ECUDA. */
+size_t fmx_adjoint_workspace_bytes(const fmx_params *p);
+fmx_status fmx_adjoint_step(fmx_grid *g, void *const *Ebar, void *const *Bbar, void *const *jbar, void *work,
+                            size_t work_bytes);
+
+/* Gaussian-envelope current on a 2D grid (a prescribed source, not part of
+ * the paper's scheme): writes j_z(i, j) = sum_p amp[p] exp(-|r_ij - c_p|^2 /
+ * (2 width^2)) (periodic distances, r_ij the node (i, j)) and j_x = j_y = 0
+ * into the bound current.  cxy: host array (x_p, y_p) pairs, amp: host array;
+ * np <= 341.  fmx_gauss_project computes out[p] = sum_ij f(i, j) G_p(i, j)
+ * for a device component array f in the grid's layout (FP64 sums; out is a
+ * host array; synchronises) -- the projection a source-amplitude gradient
+ * needs.  Errors: FMX_EINVAL, FMX_ESTATE, FMX_EUNSUPPORTED (not 2D). */
+fmx_status fmx_gauss_source(fmx_grid *g, int np, const double *cxy, const double *amp, double width);
+fmx_status fmx_gauss_project(fmx_grid *g, int np, const double *cxy, double width, const void *f, double *out);
+
 /* ---- Batched step (many independent 2D grids, one launch per step) ----
  * The grids of a batch are advanced together: every step is ONE persistent
  * kernel launch whose CTAs loop over (grid, strip, row-segment) tiles of all

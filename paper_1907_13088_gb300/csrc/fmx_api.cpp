@@ -33,6 +33,7 @@ fmx_status cuda_fail(cudaError_t e, const char *what) {
 }
 
 constexpr size_t kAlign = 256;
+constexpr size_t kSmallDoubles = 1024;  // workspace room for small per-call parameter arrays
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 double dt_cfl(const fmx_params *p) {
@@ -174,6 +175,7 @@ struct fmx_grid {
     int64_t nparts = 0;
     double *diag_out = nullptr;
     fmx::DevStatus *st = nullptr;
+    double *small = nullptr;  // kSmallDoubles doubles of workspace
     // per-kernel timing (fmx_profile_enable): events of each profiled step
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;  // reused across reads
@@ -207,6 +209,7 @@ size_t workspace_of(const fmx_params *p, int engine) {
     w += align_up((size_t)slots * 8 * sizeof(double), kAlign);
     w += align_up(8 * sizeof(double), kAlign);
     w += align_up(sizeof(fmx::DevStatus), kAlign);
+    w += align_up(kSmallDoubles * sizeof(double), kAlign);
     return w;
 }
 
@@ -401,6 +404,65 @@ fmx_status copy_rows(fmx_grid *g, void *dst, size_t dpitch, const void *src, siz
     return FMX_OK;
 }
 
+template <typename T>
+fmx_status adjoint_impl(fmx_grid *g, void *const *Eb_, void *const *Bb_, void *const *jb_, void *work,
+                        size_t work_bytes) {
+    if (g->p.iter_mode != FMX_ITER_FIXED) return fail(FMX_EUNSUPPORTED, "the adjoint covers fixed m only");
+    if (g->p.filter_target == FMX_FILTER_FIELDS && g->p.filter_passes > 0)
+        return fail(FMX_EUNSUPPORTED, "the adjoint does not cover field filtering");
+    const size_t need = workspace_of(&g->p, FMX_ENGINE_STAGED);
+    if (!work || work_bytes < need) return fail(FMX_EINVAL, "adjoint workspace of %zu bytes needed", need);
+    if ((uintptr_t)work % kAlign) return fail(FMX_EINVAL, "adjoint workspace must be 256-byte aligned");
+    T *Eb[3], *Bb[3], *jb[3];
+    for (int c = 0; c < 3; ++c) {
+        if (!Eb_[c] || !Bb_[c]) return fail(FMX_EINVAL, "NULL adjoint field");
+        Eb[c] = (T *)Eb_[c];
+        Bb[c] = (T *)Bb_[c];
+        jb[c] = jb_ ? (T *)jb_[c] : nullptr;
+    }
+    // staged layout: jf[3], tmp, dEp[3], dEa[3], dEb[3]
+    char *w = (char *)work;
+    const size_t fb = align_up(g->field_bytes, kAlign);
+    w += 4 * fb;
+    fmx::StagedPtrs<T> P;
+    for (int c = 0; c < 3; ++c) {
+        P.E[c] = nullptr;
+        P.B[c] = nullptr;
+        P.J[c] = nullptr;
+        P.jf[c] = nullptr;
+        P.dEp[c] = (T *)(w + c * fb);
+        P.dEa[c] = (T *)(w + (3 + c) * fb);
+        P.dEb[c] = (T *)(w + (6 + c) * fb);
+    }
+    P.tmp = nullptr;
+    P.partials = nullptr;
+    P.st = nullptr;
+    const fmx::Coef<T> c = make_coef<T>(g->co);
+    g->launches += fmx::launch_adj_source<T>(g->geo, g->p.dims, c, Eb, Bb, P.dEp, g->stream);
+    const T *in[3] = {P.dEp[0], P.dEp[1], P.dEp[2]};
+    for (int it = 0; it < g->p.m; ++it) {
+        T *out[3];
+        for (int q = 0; q < 3; ++q) out[q] = (it % 2 == 0) ? P.dEa[q] : P.dEb[q];
+        g->launches += fmx::launch_staged_sweep<T>(g->geo, g->p.dims, c, P, in, out, false, g->stream);
+        for (int q = 0; q < 3; ++q) in[q] = out[q];
+    }
+    T *wv[3] = {const_cast<T *>(in[0]), const_cast<T *>(in[1]), const_cast<T *>(in[2])};
+    for (int q = 0; q < 3; ++q) {
+        cudaError_t e = cudaMemcpyAsync(Eb[q], P.dEp[q], g->field_bytes, cudaMemcpyDeviceToDevice, g->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (adjoint)");
+    }
+    g->launches += fmx::launch_adj_faraday<T>(g->geo, g->p.dims, c, wv, Bb, g->stream);
+    if (jb[0]) {
+        g->launches += fmx::launch_scale_copy<T>(g->geo, -c.q, wv, jb, g->stream);
+        if (g->p.filter_target == FMX_FILTER_CURRENT && g->p.filter_passes > 0)
+            for (int q = 0; q < 3; ++q) {
+                fmx_status s = filter_in_place<T>(g, jb[q], g->p.filter_passes);
+                if (s != FMX_OK) return s;
+            }
+    }
+    return check_launch(g, "adjoint launch");
+}
+
 }  // namespace
 
 extern "C" {
@@ -475,6 +537,8 @@ fmx_status fmx_bind(fmx_grid *g, const fmx_buffers *b) {
     g->diag_out = (double *)w;
     w += align_up(8 * sizeof(double), kAlign);
     g->st = (fmx::DevStatus *)w;
+    w += align_up(sizeof(fmx::DevStatus), kAlign);
+    g->small = (double *)w;
     // status partials count for the residual reductions is one per block
     g->nparts = slots;
     cudaError_t e = cudaMemsetAsync(g->st, 0, sizeof(fmx::DevStatus), g->stream);
@@ -626,6 +690,66 @@ fmx_status fmx_sync(fmx_grid *g) {
         if (e != cudaSuccess) return cuda_fail(e, "status read-back");
         if (hs.err) return fail((fmx_status)hs.err, "device reported status %d", hs.err);
     }
+    return FMX_OK;
+}
+
+size_t fmx_adjoint_workspace_bytes(const fmx_params *p) {
+    double dt;
+    if (validate(p, &dt, nullptr) != FMX_OK) return 0;
+    return workspace_of(p, FMX_ENGINE_STAGED);
+}
+
+fmx_status fmx_adjoint_step(fmx_grid *g, void *const *Ebar, void *const *Bbar, void *const *jbar, void *work,
+                            size_t work_bytes) {
+    if (!g || !Ebar || !Bbar) return fail(FMX_EINVAL, "NULL argument");
+    if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
+    return g->p.precision == FMX_F64 ? adjoint_impl<double>(g, Ebar, Bbar, jbar, work, work_bytes)
+                                     : adjoint_impl<float>(g, Ebar, Bbar, jbar, work, work_bytes);
+}
+
+fmx_status fmx_gauss_source(fmx_grid *g, int np, const double *cxy, const double *amp, double width) {
+    if (!g || !cxy || !amp || np < 1 || !(width > 0.0)) return fail(FMX_EINVAL, "bad arguments");
+    if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
+    if (!g->buf.J[0]) return fail(FMX_ESTATE, "no J buffers bound");
+    if (g->p.dims != 2) return fail(FMX_EUNSUPPORTED, "the Gaussian source is 2D");
+    if ((size_t)np * 3 > kSmallDoubles) return fail(FMX_EINVAL, "at most %zu sources", kSmallDoubles / 3);
+    cudaError_t e = cudaMemcpyAsync(g->small, cxy, sizeof(double) * 2 * np, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->small + 2 * np, amp, sizeof(double) * np, cudaMemcpyHostToDevice, g->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "source parameter upload");
+    if (g->p.precision == FMX_F64) {
+        double *J[3] = {(double *)g->buf.J[0], (double *)g->buf.J[1], (double *)g->buf.J[2]};
+        g->launches += fmx::launch_gauss_source<double>(g->geo, np, g->small, g->small + 2 * np, width, J, g->stream);
+    } else {
+        float *J[3] = {(float *)g->buf.J[0], (float *)g->buf.J[1], (float *)g->buf.J[2]};
+        g->launches += fmx::launch_gauss_source<float>(g->geo, np, g->small, g->small + 2 * np, width, J, g->stream);
+    }
+    return check_launch(g, "Gaussian source launch");
+}
+
+fmx_status fmx_gauss_project(fmx_grid *g, int np, const double *cxy, double width, const void *f, double *out) {
+    if (!g || !cxy || !f || !out || np < 1 || !(width > 0.0)) return fail(FMX_EINVAL, "bad arguments");
+    if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
+    if (g->p.dims != 2) return fail(FMX_EUNSUPPORTED, "the Gaussian source is 2D");
+    if ((size_t)np * 3 > kSmallDoubles) return fail(FMX_EINVAL, "at most %zu sources", kSmallDoubles / 3);
+    const int64_t cap = g->nparts * 8;
+    int nblk = (int)(cap / np);
+    if (nblk > 64) nblk = 64;
+    if (nblk < 1) return fail(FMX_EINVAL, "workspace too small for %d projections", np);
+    cudaError_t e = cudaMemcpyAsync(g->small, cxy, sizeof(double) * 2 * np, cudaMemcpyHostToDevice, g->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "source parameter upload");
+    double *dout = g->small + 2 * np;
+    if (g->p.precision == FMX_F64)
+        g->launches += fmx::launch_gauss_project<double>(g->geo, np, g->small, width, (const double *)f, g->partials,
+                                                         nblk, dout, g->stream);
+    else
+        g->launches += fmx::launch_gauss_project<float>(g->geo, np, g->small, width, (const float *)f, g->partials,
+                                                        nblk, dout, g->stream);
+    fmx_status s = check_launch(g, "Gaussian projection launch");
+    if (s != FMX_OK) return s;
+    e = cudaMemcpyAsync(out, dout, sizeof(double) * np, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "projection read-back");
     return FMX_OK;
 }
 

@@ -88,4 +88,19 @@ template <typename T>
 int launch_diagnostics(const Geo &g, int dims, const Coef<double> &c, const double d[3], T *const E[3],
                        T *const B[3], double *partials, int64_t nparts, double *out_dev, cudaStream_t s);
 
+// Adjoint step and Gaussian-envelope current (adjoint.cu).
+template <typename T>
+int launch_adj_source(const Geo &g, int dims, const Coef<T> &c, T *const Eb[3], T *const Bb[3], T *const u[3],
+                      cudaStream_t s);
+template <typename T>
+int launch_adj_faraday(const Geo &g, int dims, const Coef<T> &c, T *const w[3], T *const Bb[3], cudaStream_t s);
+template <typename T>
+int launch_scale_copy(const Geo &g, T sc, T *const in[3], T *const out[3], cudaStream_t s);
+template <typename T>
+int launch_gauss_source(const Geo &g, int np, const double *cxy, const double *amp, double width, T *const J[3],
+                        cudaStream_t s);
+template <typename T>
+int launch_gauss_project(const Geo &g, int np, const double *cxy, double width, const T *f, double *partials,
+                         int nblk, double *out, cudaStream_t s);
+
 }  // namespace fmx

@@ -86,6 +86,12 @@ def _load():
         "fmx_last_error": (ctypes.c_char_p, []),
         "fmx_step_static": (ctypes.c_int, [P, vpp, vpp, vpp, ctypes.c_int]),
         "fmx_profile_enable": (ctypes.c_int, [G, ctypes.c_int]),
+        "fmx_adjoint_workspace_bytes": (ctypes.c_size_t, [P]),
+        "fmx_adjoint_step": (ctypes.c_int, [G, vpp, vpp, vpp, ctypes.c_void_p, ctypes.c_size_t]),
+        "fmx_gauss_source": (ctypes.c_int, [G, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double), ctypes.c_double]),
+        "fmx_gauss_project": (ctypes.c_int, [G, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                                             ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
         "fmx_batch_create": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(G)]),
         "fmx_batch_workspace_bytes": (ctypes.c_size_t, [G]),
         "fmx_batch_bind": (ctypes.c_int, [G, ctypes.POINTER(fmx_buffers), ctypes.c_void_p, ctypes.c_size_t]),
@@ -129,6 +135,10 @@ fmx_strerror = _lib.fmx_strerror
 fmx_last_error = _lib.fmx_last_error
 fmx_step_static = _lib.fmx_step_static
 fmx_profile_enable = _lib.fmx_profile_enable
+fmx_adjoint_workspace_bytes = _lib.fmx_adjoint_workspace_bytes
+fmx_adjoint_step = _lib.fmx_adjoint_step
+fmx_gauss_source = _lib.fmx_gauss_source
+fmx_gauss_project = _lib.fmx_gauss_project
 fmx_batch_create = _lib.fmx_batch_create
 fmx_batch_workspace_bytes = _lib.fmx_batch_workspace_bytes
 fmx_batch_bind = _lib.fmx_batch_bind

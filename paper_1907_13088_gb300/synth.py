@@ -150,3 +150,14 @@ def batch_sizes(count, seed, lo=64, hi=1024, courant_lo=0.3, courant_hi=0.9):
     ny = np.round(np.exp(rng.uniform(math.log(lo), math.log(hi), count))).astype(int)
     cf = rng.uniform(courant_lo, courant_hi, count)
     return [(int(a), int(b), float(c)) for a, b, c in zip(nx, ny, cf)]
+
+
+def gauss_sources(count, shape, seed):
+    """Centres (x_p, y_p) uniform over a 2D grid, phases U[0, 2 pi) and unit
+    normal amplitudes for `count` Gaussian-envelope current sources."""
+    rng = np.random.default_rng(seed)
+    nx, ny = int(shape[0]), int(shape[1])
+    cxy = np.stack([rng.uniform(0, nx, count), rng.uniform(0, ny, count)], axis=1)
+    phases = rng.uniform(0.0, 2.0 * math.pi, count)
+    theta = rng.standard_normal(count)
+    return cxy, phases, theta

@@ -1,0 +1,218 @@
+"""Adjoint of the step on the GPU (fmx_adjoint_step), the Gaussian-envelope
+source, and the differentiable run: against the FP64 oracle's adjoint, the
+dot-product identity, finite differences, and FP32 against FP64."""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+from oracle import core
+from paper_1907_13088_gb300 import synth
+from tests.helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fmx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_13088_gb300 import build
+    build.build()
+    from paper_1907_13088_gb300 import fmx as m
+    return m
+
+
+def _dev_pitched(a, pitch, dtype):
+    import torch
+    c, nz, ny, nx = a.shape
+    t = torch.zeros((3, nz, ny, pitch), dtype=dtype, device="cuda")
+    t[..., :nx] = torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+    return t
+
+
+def _adjoint_gpu(fmx, shape, Ebar, Bbar, **kw):
+    import torch
+    g = fmx.Grid(shape, precision=1, **kw)
+    esz, q = 8, 2
+    nx = shape[0]
+    pitch = (nx + q - 1) // q * q
+    Eb = _dev_pitched(Ebar, pitch, torch.float64)
+    Bb = _dev_pitched(Bbar, pitch, torch.float64)
+    jb = torch.zeros_like(Eb)
+    wb = fmx.fmx_adjoint_workspace_bytes(ctypes.byref(g.params))
+    work = torch.zeros(wb + 256, dtype=torch.uint8, device="cuda")
+    wp = (work.data_ptr() + 255) // 256 * 256
+    vp = lambda t: (ctypes.c_void_p * 3)(*[t[c].data_ptr() for c in range(3)])
+    fmx.check(fmx.fmx_adjoint_step(g.handle, vp(Eb), vp(Bb), vp(jb), wp, wb))
+    torch.cuda.synchronize()
+    f = lambda t: t[..., :nx].cpu().numpy()
+    return f(Eb), f(Bb), f(jb)
+
+
+@pytest.mark.parametrize("shape,kw", [((37, 29), dict(m=4, filter_passes=3)), ((12, 10, 7), dict(m=3, filter_passes=1)),
+                                      ((40,), dict(m=2, filter_passes=2)), ((16, 16), dict(m=0, filter_passes=0))])
+def test_adjoint_step_matches_oracle(fmx, shape, kw):
+    Ebar, Bbar, _ = synth.random_fields(shape, seed=41)
+    Eg, Bg, jg = _adjoint_gpu(fmx, shape, Ebar, Bbar, courant=0.7, engine=1, **kw)
+    Eo, Bo, jo = core.adjoint_step(core.Params(shape=shape, courant=0.7, **kw), Ebar, Bbar)
+    assert rel_l2(Eg, Eo) < 1e-12 and rel_l2(Bg, Bo) < 1e-12 and rel_l2(jg, jo) < 1e-12
+
+
+def test_dot_product_identity_gpu(fmx):
+    """<T d, y> = <d, T^T y> with T the GPU forward step (fused engine) and
+    T^T the GPU adjoint step."""
+    shape = (64, 48)
+    dE, dB, dJ = synth.random_fields(shape, seed=42)
+    yE, yB, _ = synth.random_fields(shape, seed=43)
+    g = fmx.Grid(shape, precision=1, m=4, filter_passes=3, engine=2)
+    g.set_fields(dE, dB)
+    g.set_current(dJ)
+    g.step(1)
+    E1, B1, _ = g.get_fields()
+    lhs = np.sum(E1 * yE) + np.sum(B1 * yB)
+    Eb, Bb, jb = _adjoint_gpu(fmx, shape, yE, yB, m=4, filter_passes=3, engine=1)
+    rhs = np.sum(dE * Eb) + np.sum(dB * Bb) + np.sum(dJ * jb)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_gauss_source_and_projection(fmx):
+    import torch
+    shape = (96, 80)
+    cxy, phases, theta = synth.gauss_sources(8, shape, seed=44)
+    w = 6.0
+    ii = np.arange(96)[None, :]
+    jj = np.arange(80)[:, None]
+    G = []
+    for x, y in cxy:
+        dx = (ii - x) - 96 * np.floor((ii - x) / 96 + 0.5)
+        dy = (jj - y) - 80 * np.floor((jj - y) / 80 + 0.5)
+        G.append(np.exp(-(dx * dx + dy * dy) / (2 * w * w)))
+    G = np.array(G)
+    g = fmx.Grid(shape, precision=1, engine=1)
+    fmx.check(fmx.fmx_gauss_source(g.handle, 8, np.ascontiguousarray(cxy).ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   theta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), w))
+    _, _, J = g.get_fields(fmx.FMX_J)
+    assert np.max(np.abs(J[:2])) == 0
+    assert rel_l2(J[2, 0], np.tensordot(theta, G, 1)) < 1e-13
+    f = np.random.default_rng(45).standard_normal((80, 96))
+    ft = torch.zeros((80, 96), dtype=torch.float64, device="cuda")
+    ft[:] = torch.from_numpy(f)
+    out = np.zeros(8)
+    fmx.check(fmx.fmx_gauss_project(g.handle, 8, np.ascontiguousarray(cxy).ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    w, ctypes.c_void_p(ft.data_ptr()), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    assert rel_l2(out, np.einsum("pij,ij->p", G, f)) < 1e-13
+
+
+def _oracle_gradient(shape, cxy, phases, theta, E0, B0, N, mask, width, omega0, **kw):
+    """dL/dtheta with the oracle alone: forward with the synthesised current,
+    then N oracle adjoint steps and the projection on the G_p."""
+    p = core.Params(shape=shape, **kw)
+    dt = p.time_step()
+    nx, ny = shape
+    ii = np.arange(nx)[None, :]
+    jj = np.arange(ny)[:, None]
+    G = []
+    for x, y in cxy:
+        dx = (ii - x) - nx * np.floor((ii - x) / nx + 0.5)
+        dy = (jj - y) - ny * np.floor((jj - y) / ny + 0.5)
+        G.append(np.exp(-(dx * dx + dy * dy) / (2 * width * width)))
+    G = np.array(G)
+    E, B = E0.copy(), B0.copy()
+    for n in range(N):
+        J = np.zeros(p.array_shape)
+        J[2, 0] = np.tensordot(theta * np.sin(omega0 * (n + 0.5) * dt + phases), G, 1)
+        E, B, _, _ = core.step(p, E, B, J, 1)
+    Eb, Bb = E * mask, B * mask
+    loss = 0.5 * (np.sum(Eb * E) + np.sum(Bb * B))
+    grad = np.zeros(len(theta))
+    for n in range(N - 1, -1, -1):
+        Eb, Bb, jb = core.adjoint_step(p, Eb, Bb)
+        grad += np.sin(omega0 * (n + 0.5) * dt + phases) * np.einsum("pij,ij->p", G, jb[2, 0])
+    return loss, grad
+
+
+def _gpu_gradient(fmx, shape, cxy, phases, theta, E0, B0, N, mask, precision, K, recompute=False, engine=0):
+    import torch
+    from paper_1907_13088_gb300.adjoint import GaussSourceRun, make_function
+    dt_ = torch.float64 if precision == 1 else torch.float32
+    run = GaussSourceRun(shape, cxy, phases, N, width=6.0, omega0=0.2, m=4, passes=3, courant=0.5,
+                         precision=precision, checkpoint_every=K, engine=engine)
+    FieldRun = make_function()
+    th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+    e0 = torch.from_numpy(np.ascontiguousarray(E0[:, 0])).to("cuda", dt_)
+    b0 = torch.from_numpy(np.ascontiguousarray(B0[:, 0])).to("cuda", dt_)
+    EN, BN = FieldRun.apply(th, e0, b0, run, recompute)
+    mk = torch.from_numpy(mask[:, 0]).to("cuda", dt_)
+    loss = 0.5 * ((EN * EN * mk).sum() + (BN * BN * mk).sum())
+    loss.backward()
+    return float(loss.detach()), th.grad.numpy().copy()
+
+
+def _setup(shape, N, seed):
+    cxy, phases, theta = synth.gauss_sources(8, shape, seed=seed)
+    E0, B0, _ = synth.random_fields(shape, seed=seed + 1)
+    E0 *= 0.01
+    B0 *= 0.01
+    mask = np.zeros((3, 1, shape[1], shape[0]))
+    mask[:, :, shape[1] // 4:shape[1] // 2, shape[0] // 4:shape[0] // 2] = 1.0
+    return cxy, phases, theta, E0, B0, mask
+
+
+def test_autograd_gradient_matches_oracle_fp64(fmx):
+    shape, N = (96, 80), 24
+    cxy, phases, theta, E0, B0, mask = _setup(shape, N, 46)
+    lo, go = _oracle_gradient(shape, cxy, phases, theta, E0, B0, N, mask, 6.0, 0.2, courant=0.5, m=4,
+                              filter_passes=3)
+    for engine, recompute in ((2, False), (1, True)):
+        lg, gg = _gpu_gradient(fmx, shape, cxy, phases, theta, E0, B0, N, mask, 1, K=5, recompute=recompute,
+                               engine=engine)
+        assert abs(lg - lo) <= 1e-12 * abs(lo)
+        assert rel_l2(gg, go) < 1e-11
+
+
+def test_autograd_central_differences_fp64(fmx):
+    """Central differences (eps = 1e-3) of the GPU FP64 loss along seeded
+    directions against the adjoint gradient (the loss is quadratic in theta,
+    so the differences are exact up to round-off)."""
+    shape, N = (128, 96), 30
+    cxy, phases, theta, E0, B0, mask = _setup(shape, N, 47)
+    l0, g0 = _gpu_gradient(fmx, shape, cxy, phases, theta, E0, B0, N, mask, 1, K=10, engine=2)
+    rng = np.random.default_rng(48)
+    eps = 1e-3
+    for _ in range(3):
+        d = rng.standard_normal(len(theta))
+        lp, _ = _gpu_gradient(fmx, shape, cxy, phases, theta + eps * d, E0, B0, N, mask, 1, K=10, engine=2)
+        lm, _ = _gpu_gradient(fmx, shape, cxy, phases, theta - eps * d, E0, B0, N, mask, 1, K=10, engine=2)
+        fd = (lp - lm) / (2 * eps)
+        assert abs(fd - g0 @ d) <= 1e-8 * max(abs(fd), 1e-30)
+
+
+@pytest.mark.slow
+def test_fp32_gradient_1024_against_fp64(fmx):
+    """The 1024^2 FP32 run (64 sources, checkpoint every 50 steps) against the
+    same run in FP64: relative error of dL/dtheta stated and bounded."""
+    from paper_1907_13088_gb300.adjoint import GaussSourceRun
+    shape, N = (1024, 1024), 100
+    cxy, phases, theta = synth.gauss_sources(64, shape, seed=1907005)
+    E0, B0, _ = synth.random_fields(shape, seed=1907006)
+    E0 *= 0.01
+    B0 *= 0.01
+    mask = np.zeros((3, 1, 1024, 1024))
+    mask[:, :, 448:576, 448:576] = 1.0
+    grads = []
+    for prec in (1, 0):
+        import torch
+        from paper_1907_13088_gb300.adjoint import make_function
+        dt_ = torch.float64 if prec == 1 else torch.float32
+        run = GaussSourceRun(shape, cxy, phases, N, width=8.0, omega0=0.2, m=4, passes=3, courant=0.5,
+                             precision=prec, checkpoint_every=50)
+        th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+        EN, BN = make_function().apply(th, torch.from_numpy(E0[:, 0]).to("cuda", dt_),
+                                       torch.from_numpy(B0[:, 0]).to("cuda", dt_), run, False)
+        mk = torch.from_numpy(mask[:, 0]).to("cuda", dt_)
+        (0.5 * ((EN * EN * mk).sum() + (BN * BN * mk).sum())).backward()
+        grads.append(th.grad.numpy().copy())
+    assert rel_l2(grads[1], grads[0]) < 1e-3
