@@ -236,12 +236,19 @@ fmx_status fmx_adjoint_step(fmx_grid *g, void *const *Ebar, void *const *Bbar, v
  * the paper's scheme): writes j_z(i, j) = sum_p amp[p] exp(-|r_ij - c_p|^2 /
  * (2 width^2)) (periodic distances, r_ij the node (i, j)) and j_x = j_y = 0
  * into the bound current.  cxy: host array (x_p, y_p) pairs, amp: host array;
- * np <= 341.  fmx_gauss_project computes out[p] = sum_ij f(i, j) G_p(i, j)
+ * np <= 128.  fmx_gauss_project computes out[p] = sum_ij f(i, j) G_p(i, j)
  * for a device component array f in the grid's layout (FP64 sums; out is a
  * host array; synchronises) -- the projection a source-amplitude gradient
- * needs.  Errors: FMX_EINVAL, FMX_ESTATE, FMX_EUNSUPPORTED (not 2D). */
+ * needs.  fmx_gauss_accumulate adds weights[p] * sum_ij f G_p to a device
+ * accumulator (reset != 0 zeroes it first; asynchronous) and
+ * fmx_gauss_accumulated copies the accumulator to out (synchronises).  The
+ * host arrays are read before the call returns.  Errors: FMX_EINVAL,
+ * FMX_ESTATE, FMX_EUNSUPPORTED (not 2D). */
 fmx_status fmx_gauss_source(fmx_grid *g, int np, const double *cxy, const double *amp, double width);
 fmx_status fmx_gauss_project(fmx_grid *g, int np, const double *cxy, double width, const void *f, double *out);
+fmx_status fmx_gauss_accumulate(fmx_grid *g, int np, const double *cxy, double width, const void *f,
+                                const double *weights, int reset);
+fmx_status fmx_gauss_accumulated(fmx_grid *g, int np, double *out);
 
 /* ---- Batched step (many independent 2D grids, one launch per step) ----
  * The grids of a batch are advanced together: every step is ONE persistent

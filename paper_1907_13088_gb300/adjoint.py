@@ -102,7 +102,8 @@ class GaussSourceRun:
         self.Ebar[:, :, :nx].copy_(gE)
         self.Bbar[:, :, :nx].copy_(gB)
         grad = np.zeros(self.np_)
-        proj = np.zeros(self.np_)
+        first = True
+        cptr = self.cxy.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         starts = sorted(self.checkpoints)
         l0 = g.launches
         for si in range(len(starts) - 1, -1, -1):
@@ -120,13 +121,16 @@ class GaussSourceRun:
                         self.torch.equal(B1, self.checkpoints[s1][1]), "recomputed segment left its checkpoint"
             for n in range(s1 - 1, s0 - 1, -1):
                 self._adjoint_step(nx)
-                fmx.check(fmx.fmx_gauss_project(g.handle, self.np_,
-                                                self.cxy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                                self.width, ctypes.c_void_p(self.jbar[2].data_ptr()),
-                                                proj.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
-                          "fmx_gauss_project")
                 t = (n + 0.5) * self.dt
-                grad += np.sin(self.omega0 * t + self.phases) * proj
+                wts = np.ascontiguousarray(np.sin(self.omega0 * t + self.phases))
+                fmx.check(fmx.fmx_gauss_accumulate(g.handle, self.np_, cptr, self.width,
+                                                   ctypes.c_void_p(self.jbar[2].data_ptr()),
+                                                   wts.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                   int(first)), "fmx_gauss_accumulate")
+                first = False
+        if not first:
+            fmx.check(fmx.fmx_gauss_accumulated(g.handle, self.np_, grad.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                      "fmx_gauss_accumulated")
         self.launches += g.launches - l0
         return grad, self.Ebar[:, :, :nx].clone(), self.Bbar[:, :, :nx].clone()
 

@@ -81,10 +81,17 @@ __global__ void k_scale_copy(Geo g, T s, const T *i0, const T *i1, const T *i2, 
 }
 
 // Gaussian-envelope current: j_z(i, j) = sum_p amp_p exp(-|r_ij - c_p|^2 / (2 w^2)),
-// distances taken periodically; 2D, j_z sits on the node (i, j).
-__device__ __forceinline__ double pdist(double d, double n) {
-    d -= n * floor(d / n + 0.5);
-    return d;
+// distances taken periodically; 2D, j_z sits on the node (i, j).  The
+// arithmetic is in the storage precision T.
+template <typename T>
+__device__ __forceinline__ T pdist(T d, T n) {
+    return d - n * floor(d / n + T(0.5));
+}
+
+template <typename T>
+__device__ __forceinline__ T gexp(T e) {
+    if constexpr (sizeof(T) == 4) return __expf(e);
+    else return exp(e);
 }
 
 template <typename T>
@@ -93,32 +100,31 @@ __global__ void k_gauss_source(Geo g, int np, const double *cxy, const double *a
     Pos p;
     int64_t idx;
     if (!cell_of(g, p, idx)) return;
+    const T nx = (T)g.nx, ny = (T)g.ny, k = (T)inv2w2;
     T acc = T(0);
     for (int q = 0; q < np; ++q) {
-        const double dx = pdist((double)p.i - cxy[2 * q], (double)g.nx);
-        const double dy = pdist((double)p.j - cxy[2 * q + 1], (double)g.ny);
-        const T e = (T)(-(dx * dx + dy * dy) * inv2w2);
-        acc += (T)amp[q] * (sizeof(T) == 4 ? (T)__expf((float)e) : (T)exp((double)e));
+        const T dx = pdist<T>((T)p.i - (T)cxy[2 * q], nx);
+        const T dy = pdist<T>((T)p.j - (T)cxy[2 * q + 1], ny);
+        acc += (T)amp[q] * gexp<T>(-(dx * dx + dy * dy) * k);
     }
     jx[idx] = T(0);
     jy[idx] = T(0);
     jz[idx] = acc;
 }
 
-// partials[q * nblk + b] = sum over the cells of block b of f * G_q (FP64)
+// partials[q * nblk + b] = sum over the cells of block b of f * G_q (G in the
+// storage precision, sums in FP64)
 template <typename T>
 __global__ void k_gauss_project(Geo g, int np, const double *cxy, double inv2w2, const T *f, double *partials,
                                 int nblk) {
     const int q = blockIdx.y;
     const int64_t ncell = (int64_t)g.nx * g.ny;
+    const T nx = (T)g.nx, ny = (T)g.ny, k = (T)inv2w2, cx = (T)cxy[2 * q], cy = (T)cxy[2 * q + 1];
     double acc = 0.0;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += (int64_t)nblk * blockDim.x) {
         const int i = (int)(c % g.nx), j = (int)(c / g.nx);
-        const double dx = pdist((double)i - cxy[2 * q], (double)g.nx);
-        const double dy = pdist((double)j - cxy[2 * q + 1], (double)g.ny);
-        const double e = -(dx * dx + dy * dy) * inv2w2;
-        const double gv = sizeof(T) == 4 ? (double)__expf((float)e) : exp(e);
-        acc += (double)f[(int64_t)j * g.pitch + i] * gv;
+        const T dx = pdist<T>((T)i - cx, nx), dy = pdist<T>((T)j - cy, ny);
+        acc += (double)(f[(int64_t)j * g.pitch + i] * gexp<T>(-(dx * dx + dy * dy) * k));
     }
     __shared__ double red[32];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -131,12 +137,14 @@ __global__ void k_gauss_project(Geo g, int np, const double *cxy, double inv2w2,
     }
 }
 
-__global__ void k_gauss_project_final(const double *partials, int nblk, int np, double *out) {
+// out[q] = sum_b partials (weights == nullptr), or acc[q] += weights[q] * sum_b partials
+__global__ void k_gauss_project_final(const double *partials, int nblk, int np, const double *weights, double *out) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= np) return;
     double s = 0.0;
     for (int b = 0; b < nblk; ++b) s += partials[(int64_t)q * nblk + b];
-    out[q] = s;
+    if (weights) out[q] += weights[q] * s;
+    else out[q] = s;
 }
 
 }  // namespace
@@ -182,9 +190,9 @@ int launch_gauss_source(const Geo &g, int np, const double *cxy, const double *a
 
 template <typename T>
 int launch_gauss_project(const Geo &g, int np, const double *cxy, double width, const T *f, double *partials,
-                         int nblk, double *out, cudaStream_t s) {
+                         int nblk, const double *weights, double *out, cudaStream_t s) {
     k_gauss_project<T><<<dim3(nblk, np), 256, 0, s>>>(g, np, cxy, 1.0 / (2.0 * width * width), f, partials, nblk);
-    k_gauss_project_final<<<(np + 127) / 128, 128, 0, s>>>(partials, nblk, np, out);
+    k_gauss_project_final<<<(np + 127) / 128, 128, 0, s>>>(partials, nblk, np, weights, out);
     return 2;
 }
 
@@ -196,7 +204,7 @@ int launch_gauss_project(const Geo &g, int np, const double *cxy, double width, 
     template int launch_gauss_source<T>(const Geo &, int, const double *, const double *, double, T *const[3],  \
                                         cudaStream_t);                                                         \
     template int launch_gauss_project<T>(const Geo &, int, const double *, double, const T *, double *, int,    \
-                                         double *, cudaStream_t);
+                                         const double *, double *, cudaStream_t);
 FMX_ADJ_INST(float)
 FMX_ADJ_INST(double)
 #undef FMX_ADJ_INST

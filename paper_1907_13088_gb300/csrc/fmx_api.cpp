@@ -712,7 +712,7 @@ fmx_status fmx_gauss_source(fmx_grid *g, int np, const double *cxy, const double
     if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
     if (!g->buf.J[0]) return fail(FMX_ESTATE, "no J buffers bound");
     if (g->p.dims != 2) return fail(FMX_EUNSUPPORTED, "the Gaussian source is 2D");
-    if ((size_t)np * 3 > kSmallDoubles) return fail(FMX_EINVAL, "at most %zu sources", kSmallDoubles / 3);
+    if ((size_t)np * 4 > kSmallDoubles / 2) return fail(FMX_EINVAL, "at most %zu sources", kSmallDoubles / 8);
     cudaError_t e = cudaMemcpyAsync(g->small, cxy, sizeof(double) * 2 * np, cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g->small + 2 * np, amp, sizeof(double) * np, cudaMemcpyHostToDevice, g->stream);
@@ -727,29 +727,62 @@ fmx_status fmx_gauss_source(fmx_grid *g, int np, const double *cxy, const double
     return check_launch(g, "Gaussian source launch");
 }
 
-fmx_status fmx_gauss_project(fmx_grid *g, int np, const double *cxy, double width, const void *f, double *out) {
-    if (!g || !cxy || !f || !out || np < 1 || !(width > 0.0)) return fail(FMX_EINVAL, "bad arguments");
+// small-region layout: [0, 2np) centres, [2np, 3np) amplitudes or weights,
+// [3np, 4np) projection output, [kSmallDoubles/2, +np) accumulator
+static fmx_status gauss_project_impl(fmx_grid *g, int np, const double *cxy, double width, const void *f,
+                                     const double *weights, double *out_host) {
+    if (!g || !cxy || !f || np < 1 || !(width > 0.0)) return fail(FMX_EINVAL, "bad arguments");
     if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
     if (g->p.dims != 2) return fail(FMX_EUNSUPPORTED, "the Gaussian source is 2D");
-    if ((size_t)np * 3 > kSmallDoubles) return fail(FMX_EINVAL, "at most %zu sources", kSmallDoubles / 3);
+    if ((size_t)np * 4 > kSmallDoubles / 2) return fail(FMX_EINVAL, "at most %zu sources", kSmallDoubles / 8);
     const int64_t cap = g->nparts * 8;
     int nblk = (int)(cap / np);
     if (nblk > 64) nblk = 64;
     if (nblk < 1) return fail(FMX_EINVAL, "workspace too small for %d projections", np);
     cudaError_t e = cudaMemcpyAsync(g->small, cxy, sizeof(double) * 2 * np, cudaMemcpyHostToDevice, g->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "source parameter upload");
-    double *dout = g->small + 2 * np;
+    if (e == cudaSuccess && weights)
+        e = cudaMemcpyAsync(g->small + 2 * np, weights, sizeof(double) * np, cudaMemcpyHostToDevice, g->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "projection parameter upload");
+    const double *w = weights ? g->small + 2 * np : nullptr;
+    double *dout = weights ? g->small + kSmallDoubles / 2 : g->small + 3 * np;
     if (g->p.precision == FMX_F64)
         g->launches += fmx::launch_gauss_project<double>(g->geo, np, g->small, width, (const double *)f, g->partials,
-                                                         nblk, dout, g->stream);
+                                                         nblk, w, dout, g->stream);
     else
         g->launches += fmx::launch_gauss_project<float>(g->geo, np, g->small, width, (const float *)f, g->partials,
-                                                        nblk, dout, g->stream);
+                                                        nblk, w, dout, g->stream);
     fmx_status s = check_launch(g, "Gaussian projection launch");
-    if (s != FMX_OK) return s;
-    e = cudaMemcpyAsync(out, dout, sizeof(double) * np, cudaMemcpyDeviceToHost, g->stream);
+    if (s != FMX_OK || !out_host) return s;
+    e = cudaMemcpyAsync(out_host, dout, sizeof(double) * np, cudaMemcpyDeviceToHost, g->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return cuda_fail(e, "projection read-back");
+    return FMX_OK;
+}
+
+fmx_status fmx_gauss_project(fmx_grid *g, int np, const double *cxy, double width, const void *f, double *out) {
+    if (!out) return fail(FMX_EINVAL, "NULL output");
+    return gauss_project_impl(g, np, cxy, width, f, nullptr, out);
+}
+
+fmx_status fmx_gauss_accumulate(fmx_grid *g, int np, const double *cxy, double width, const void *f,
+                                const double *weights, int reset) {
+    if (!g || !weights) return fail(FMX_EINVAL, "NULL argument");
+    if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
+    if ((size_t)np * 4 > kSmallDoubles / 2) return fail(FMX_EINVAL, "at most %zu sources", kSmallDoubles / 8);
+    if (reset) {
+        cudaError_t e = cudaMemsetAsync(g->small + kSmallDoubles / 2, 0, sizeof(double) * np, g->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    }
+    return gauss_project_impl(g, np, cxy, width, f, weights, nullptr);
+}
+
+fmx_status fmx_gauss_accumulated(fmx_grid *g, int np, double *out) {
+    if (!g || !out || np < 1) return fail(FMX_EINVAL, "bad arguments");
+    if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
+    cudaError_t e = cudaMemcpyAsync(out, g->small + kSmallDoubles / 2, sizeof(double) * np, cudaMemcpyDeviceToHost,
+                                    g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "accumulator read-back");
     return FMX_OK;
 }
 

@@ -101,6 +101,6 @@ int launch_gauss_source(const Geo &g, int np, const double *cxy, const double *a
                         cudaStream_t s);
 template <typename T>
 int launch_gauss_project(const Geo &g, int np, const double *cxy, double width, const T *f, double *partials,
-                         int nblk, double *out, cudaStream_t s);
+                         int nblk, const double *weights, double *out, cudaStream_t s);
 
 }  // namespace fmx

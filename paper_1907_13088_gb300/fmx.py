@@ -92,6 +92,9 @@ def _load():
                                             ctypes.POINTER(ctypes.c_double), ctypes.c_double]),
         "fmx_gauss_project": (ctypes.c_int, [G, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
                                              ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+        "fmx_gauss_accumulate": (ctypes.c_int, [G, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                                                ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+        "fmx_gauss_accumulated": (ctypes.c_int, [G, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "fmx_batch_create": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(G)]),
         "fmx_batch_workspace_bytes": (ctypes.c_size_t, [G]),
         "fmx_batch_bind": (ctypes.c_int, [G, ctypes.POINTER(fmx_buffers), ctypes.c_void_p, ctypes.c_size_t]),
@@ -139,6 +142,8 @@ fmx_adjoint_workspace_bytes = _lib.fmx_adjoint_workspace_bytes
 fmx_adjoint_step = _lib.fmx_adjoint_step
 fmx_gauss_source = _lib.fmx_gauss_source
 fmx_gauss_project = _lib.fmx_gauss_project
+fmx_gauss_accumulate = _lib.fmx_gauss_accumulate
+fmx_gauss_accumulated = _lib.fmx_gauss_accumulated
 fmx_batch_create = _lib.fmx_batch_create
 fmx_batch_workspace_bytes = _lib.fmx_batch_workspace_bytes
 fmx_batch_bind = _lib.fmx_batch_bind

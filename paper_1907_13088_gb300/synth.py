@@ -69,13 +69,22 @@ def tm_plane_waves(shape, dt, nmodes=8, kmax=8, seed=1907001, c=1.0, d=(1.0, 1.0
     return E, B, modes
 
 
+def _ifftn(F):
+    try:  # multithreaded when scipy is present; the same transform otherwise
+        import os
+        import scipy.fft
+        return scipy.fft.ifftn(F, workers=os.cpu_count() or 1)
+    except ImportError:
+        return np.fft.ifftn(F)
+
+
 def _spectrum_plane(rng, shape, weight, dtype):
     """One real field, sum over all DFT modes with |amplitude| = weight(n) and
     uniformly random phases, normalised to unit RMS."""
     nx, ny, nz = shape
     ph = rng.uniform(0.0, 2.0 * math.pi, size=(nz, ny, nx)).astype(np.float32)
     F = (weight * np.exp(1j * ph)).astype(np.complex64)
-    f = np.fft.ifftn(F).real
+    f = _ifftn(F).real
     rms = float(np.sqrt(np.mean(f.astype(np.float64) ** 2)))
     return (f / rms).astype(dtype) if rms > 0 else f.astype(dtype)
 
