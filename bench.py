@@ -16,7 +16,6 @@ grid (independent replicas, weak scaling, no collective on the data path).
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import math
 import os
@@ -65,14 +64,6 @@ def _peaks():
     return FALLBACK_HBM_GBS, "fallback (6.8 TB/s, no MEASURED_PEAKS.json)"
 
 
-def _kernel_hash():
-    h = hashlib.sha256()
-    for name in ("fused2d_pol.cu", "fused2d.h", "fmx_internal.h"):
-        with open(os.path.join(ROOT, "paper_1907_13088_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
-    return h.hexdigest()[:16]
-
-
 def _ncu_traffic(kernel_name):
     """dram bytes (read + write) per launch of a kernel from the committed ncu
     summary, or None when absent or taken on another version of the kernel."""
@@ -82,7 +73,8 @@ def _ncu_traffic(kernel_name):
     try:
         with open(path) as f:
             d = json.load(f)
-        if d.get("kernel_sha256_16") != _kernel_hash():
+        from paper_1907_13088_gb300.ncu_report import kernel_hash
+        if d.get("kernel_sha256_16") != kernel_hash():
             return None
         return float(d["dram_bytes_per_launch"][kernel_name])
     except Exception:

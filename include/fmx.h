@@ -250,6 +250,29 @@ fmx_status fmx_gauss_accumulate(fmx_grid *g, int np, const double *cxy, double w
                                 const double *weights, int reset);
 fmx_status fmx_gauss_accumulated(fmx_grid *g, int np, double *out);
 
+/* Gaussian-source run: the differentiable workload's forward and reverse
+ * loops, enqueued on the grid's stream without host synchronisation.
+ * fmx_gauss_setup stores np <= 128 sources: centres cxy ((x_p, y_p) pairs),
+ * amplitudes theta, phases phi (host arrays, copied before the call returns),
+ * the envelope width and the angular frequency omega0.
+ * fmx_gauss_run enqueues, for n = n0 .. n0 + nsteps - 1, the current
+ *   j_z = sum_p theta_p sin(omega0 (n + 1/2) dt + phi_p) G_p,  j_x = j_y = 0,
+ * (G_p as for fmx_gauss_source) followed by one fmx_step.
+ * fmx_gauss_adjoint_run enqueues, for n = n0 + nsteps - 1 down to n0, one
+ * fmx_adjoint_step (Ebar, Bbar updated in place; jbar[2]: device array in the
+ * grid's layout that receives dL/dj_z, jbar[0], jbar[1] untouched) followed by
+ *   acc_p += sin(omega0 (n + 1/2) dt + phi_p) sum_ij jbar_z(i, j) G_p(i, j);
+ * reset != 0 zeroes acc first.  With Ebar, Bbar starting as dL/d(E^N,
+ * B^{N+1/2}) and n0 = 0, nsteps = N, fmx_gauss_accumulated then returns
+ * dL/dtheta.  work: as for fmx_adjoint_step.  Errors: FMX_EINVAL, FMX_ESTATE
+ * (not bound, no current buffers, no set-up), FMX_EUNSUPPORTED (not 2D; the
+ * adjoint's own restrictions), FMX_ECUDA. */
+fmx_status fmx_gauss_setup(fmx_grid *g, int np, const double *cxy, const double *theta, const double *phi,
+                           double width, double omega0);
+fmx_status fmx_gauss_run(fmx_grid *g, int64_t n0, int nsteps);
+fmx_status fmx_gauss_adjoint_run(fmx_grid *g, int64_t n0, int nsteps, void *const *Ebar, void *const *Bbar,
+                                 void *const *jbar, void *work, size_t work_bytes, int reset);
+
 /* ---- Batched step (many independent 2D grids, one launch per step) ----
  * The grids of a batch are advanced together: every step is ONE persistent
  * kernel launch whose CTAs loop over (grid, strip, row-segment) tiles of all

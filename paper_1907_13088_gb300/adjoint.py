@@ -2,9 +2,11 @@
 
 j_z^{n+1/2}(r) = sum_p theta_p sin(omega0 (n + 1/2) dt + phi_p) G_p(r),
 G_p(r) = exp(-|r - c_p|^2 / (2 w^2)), on a 2D periodic grid.  The forward
-pass runs N steps through the C ABI (source synthesis + fmx_step); the
-backward pass runs N adjoint steps (fmx_adjoint_step, the hand-written
-transpose of the step) and projects dL/dj_z on the G_p (fmx_gauss_project).
+pass runs N steps through the C ABI (fmx_gauss_run: source synthesis from
+theta and the phases on the device, then the step); the backward pass runs N
+adjoint steps (fmx_gauss_adjoint_run: fmx_adjoint_step, the hand-written
+transpose of the step, then the projection of dL/dj_z on the G_p, weighted
+and accumulated on the device).
 
 Checkpointing: the forward keeps the state every `checkpoint_every` steps,
 O(N / K) states, and the backward walks the segments in reverse.  The step
@@ -16,7 +18,6 @@ where a state-dependent step would take its linearisation point.
 from __future__ import annotations
 
 import ctypes
-import math
 
 import numpy as np
 
@@ -56,41 +57,34 @@ class GaussSourceRun:
         self.launches = 0
 
     # ------------------------------------------------------------------
-    def amplitudes(self, theta, n):
-        t = (n + 0.5) * self.dt
-        return np.asarray(theta, dtype=np.float64) * np.sin(self.omega0 * t + self.phases)
-
-    def _set_source(self, theta, n):
-        a = np.ascontiguousarray(self.amplitudes(theta, n))
-        fmx.check(fmx.fmx_gauss_source(self.grid.handle, self.np_,
-                                       self.cxy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                       a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.width),
-                  "fmx_gauss_source")
-
     def _state(self):
         out = self.torch.empty((9, 1) + self.shape[::-1], dtype=self.grid.dtype, device=self.grid.device)
         E, B, _ = self.grid.get_fields(fmx.FMX_E | fmx.FMX_B, out=out)
         return E[:, 0].clone(), B[:, 0].clone()
 
+    def _setup(self, theta):
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+        dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        fmx.check(fmx.fmx_gauss_setup(self.grid.handle, self.np_, dp(self.cxy), dp(th),
+                                      dp(np.ascontiguousarray(self.phases)), self.width, self.omega0),
+                  "fmx_gauss_setup")
+
     def forward(self, theta, E0, B0):
         """E0, B0: device tensors (3, ny, nx).  Returns (E^N, B^N) and keeps
-        the checkpoints (state before steps 0, K, 2K, ...)."""
+        the checkpoints (state before steps 0, K, 2K, ...).  Each segment of
+        K steps is one fmx_gauss_run call (source synthesis and step on the
+        device, no host synchronisation inside)."""
         g = self.grid
         g.set_fields(E0.reshape((3, 1) + E0.shape[1:]), B0.reshape((3, 1) + B0.shape[1:]))
+        self._setup(theta)
         self.checkpoints = {}
         l0 = g.launches
-        for n in range(self.nsteps):
-            if n % self.K == 0:
-                self.checkpoints[n] = self._state()
-            self._set_source(theta, n)
-            g.step(1)
+        for n in range(0, self.nsteps, self.K):
+            self.checkpoints[n] = self._state()
+            k = min(self.K, self.nsteps - n)
+            fmx.check(fmx.fmx_gauss_run(g.handle, n, k), "fmx_gauss_run")
         self.launches += g.launches - l0
         return self._state()
-
-    def _adjoint_step(self, nx):
-        vp = lambda t: (ctypes.c_void_p * 3)(*[t[c].data_ptr() for c in range(3)])
-        fmx.check(fmx.fmx_adjoint_step(self.grid.handle, vp(self.Ebar), vp(self.Bbar), vp(self.jbar),
-                                       self._awork_ptr, self._awork_bytes), "fmx_adjoint_step")
 
     def backward(self, theta, gE, gB, recompute=False):
         """gE, gB = dL/d(E^N, B^N) (device tensors (3, ny, nx)).  Returns
@@ -102,8 +96,8 @@ class GaussSourceRun:
         self.Ebar[:, :, :nx].copy_(gE)
         self.Bbar[:, :, :nx].copy_(gB)
         grad = np.zeros(self.np_)
-        first = True
-        cptr = self.cxy.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        self._setup(theta)
+        vp = lambda t: (ctypes.c_void_p * 3)(*[t[c].data_ptr() for c in range(3)])
         starts = sorted(self.checkpoints)
         l0 = g.launches
         for si in range(len(starts) - 1, -1, -1):
@@ -112,23 +106,15 @@ class GaussSourceRun:
             if recompute:
                 E, B = self.checkpoints[s0]
                 g.set_fields(E.reshape((3, 1, ny, nx)), B.reshape((3, 1, ny, nx)))
-                for n in range(s0, s1):
-                    self._set_source(theta, n)
-                    g.step(1)
+                fmx.check(fmx.fmx_gauss_run(g.handle, s0, s1 - s0), "fmx_gauss_run")
                 if s1 in self.checkpoints:
                     E1, B1 = self._state()
                     assert self.torch.equal(E1, self.checkpoints[s1][0]) and \
                         self.torch.equal(B1, self.checkpoints[s1][1]), "recomputed segment left its checkpoint"
-            for n in range(s1 - 1, s0 - 1, -1):
-                self._adjoint_step(nx)
-                t = (n + 0.5) * self.dt
-                wts = np.ascontiguousarray(np.sin(self.omega0 * t + self.phases))
-                fmx.check(fmx.fmx_gauss_accumulate(g.handle, self.np_, cptr, self.width,
-                                                   ctypes.c_void_p(self.jbar[2].data_ptr()),
-                                                   wts.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                                   int(first)), "fmx_gauss_accumulate")
-                first = False
-        if not first:
+            fmx.check(fmx.fmx_gauss_adjoint_run(g.handle, s0, s1 - s0, vp(self.Ebar), vp(self.Bbar), vp(self.jbar),
+                                                self._awork_ptr, self._awork_bytes, int(si == len(starts) - 1)),
+                      "fmx_gauss_adjoint_run")
+        if starts:
             fmx.check(fmx.fmx_gauss_accumulated(g.handle, self.np_, grad.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
                       "fmx_gauss_accumulated")
         self.launches += g.launches - l0

@@ -75,14 +75,22 @@ __global__ void k_scale_copy(Geo g, T s, const T *i0, const T *i1, const T *i2, 
     Pos p;
     int64_t idx;
     if (!cell_of(g, p, idx)) return;
-    o0[idx] = s * i0[idx];
-    o1[idx] = s * i1[idx];
-    o2[idx] = s * i2[idx];
+    // a null output component is skipped (callers may want only some)
+    if (o0) o0[idx] = s * i0[idx];
+    if (o1) o1[idx] = s * i1[idx];
+    if (o2) o2[idx] = s * i2[idx];
 }
 
-// Gaussian-envelope current: j_z(i, j) = sum_p amp_p exp(-|r_ij - c_p|^2 / (2 w^2)),
-// distances taken periodically; 2D, j_z sits on the node (i, j).  The
-// arithmetic is in the storage precision T.
+// Gaussian-envelope current: j_z(i, j) = sum_p a_p G_p(i, j) with
+// G_p = exp(-|r_ij - c_p|^2 / (2 w^2)), distances taken periodically per axis;
+// 2D, j_z sits on the node (i, j).  The envelope factorises per axis,
+// G_p(i, j) = gx_p(i) gy_p(j), so a tile of GTX columns x GTY rows needs
+// np (GTX + GTY) exponentials instead of np GTX GTY: the tile's 1D profiles
+// go to shared memory and every cell is a sum of np products.  Amplitudes
+// are given (amp) or formed in the kernel as a_p = theta_p sin(omega0 t +
+// phi_p) (FP64).  The arithmetic is otherwise in the storage precision T.
+constexpr int GTX = 32, GTY = 64, GRY = 8;  // tile; rows per thread (256 threads)
+
 template <typename T>
 __device__ __forceinline__ T pdist(T d, T n) {
     return d - n * floor(d / n + T(0.5));
@@ -94,56 +102,124 @@ __device__ __forceinline__ T gexp(T e) {
     else return exp(e);
 }
 
+struct GaussArgs {
+    const double *cxy;    // (x_p, y_p)
+    const double *amp;    // a_p, or nullptr: theta, phi, omega0, t below
+    const double *theta;
+    const double *phi;
+    double omega0, t;
+    double inv2w2;        // 1 / (2 w^2)
+    int np;
+};
+
+// shared layout: gx[np][GTX], gy[np][GTY] (gy pre-scaled by a_p in the source)
 template <typename T>
-__global__ void k_gauss_source(Geo g, int np, const double *cxy, const double *amp, double inv2w2, T *jx, T *jy,
-                               T *jz) {
-    Pos p;
-    int64_t idx;
-    if (!cell_of(g, p, idx)) return;
-    const T nx = (T)g.nx, ny = (T)g.ny, k = (T)inv2w2;
-    T acc = T(0);
-    for (int q = 0; q < np; ++q) {
-        const T dx = pdist<T>((T)p.i - (T)cxy[2 * q], nx);
-        const T dy = pdist<T>((T)p.j - (T)cxy[2 * q + 1], ny);
-        acc += (T)amp[q] * gexp<T>(-(dx * dx + dy * dy) * k);
+__device__ __forceinline__ void gauss_profiles(const Geo &g, const GaussArgs &a, int x0, int y0, bool scale, T *gx,
+                                               T *gy) {
+    const T nx = (T)g.nx, ny = (T)g.ny, k = (T)a.inv2w2;
+    for (int q = threadIdx.x; q < a.np * GTX; q += blockDim.x) {
+        const int p = q / GTX, i = x0 + q % GTX;
+        const T dx = pdist<T>((T)i - (T)a.cxy[2 * p], nx);
+        gx[q] = gexp<T>(-dx * dx * k);
     }
-    jx[idx] = T(0);
-    jy[idx] = T(0);
-    jz[idx] = acc;
+    for (int q = threadIdx.x; q < a.np * GTY; q += blockDim.x) {
+        const int p = q / GTY, j = y0 + q % GTY;
+        const T dy = pdist<T>((T)j - (T)a.cxy[2 * p + 1], ny);
+        T v = gexp<T>(-dy * dy * k);
+        if (scale) {
+            const double amp = a.amp ? a.amp[p] : a.theta[p] * sin(a.omega0 * a.t + a.phi[p]);
+            v *= (T)amp;
+        }
+        gy[q] = v;
+    }
 }
 
-// partials[q * nblk + b] = sum over the cells of block b of f * G_q (G in the
-// storage precision, sums in FP64)
 template <typename T>
-__global__ void k_gauss_project(Geo g, int np, const double *cxy, double inv2w2, const T *f, double *partials,
-                                int nblk) {
-    const int q = blockIdx.y;
-    const int64_t ncell = (int64_t)g.nx * g.ny;
-    const T nx = (T)g.nx, ny = (T)g.ny, k = (T)inv2w2, cx = (T)cxy[2 * q], cy = (T)cxy[2 * q + 1];
-    double acc = 0.0;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += (int64_t)nblk * blockDim.x) {
-        const int i = (int)(c % g.nx), j = (int)(c / g.nx);
-        const T dx = pdist<T>((T)i - cx, nx), dy = pdist<T>((T)j - cy, ny);
-        acc += (double)(f[(int64_t)j * g.pitch + i] * gexp<T>(-(dx * dx + dy * dy) * k));
-    }
-    __shared__ double red[32];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+__global__ void __launch_bounds__(256) k_gauss_source(Geo g, GaussArgs a, T *jx, T *jy, T *jz, int zero_xy) {
+    extern __shared__ __align__(16) unsigned char gsm[];
+    T *gx = reinterpret_cast<T *>(gsm);
+    T *gy = gx + a.np * GTX;
+    const int x0 = blockIdx.x * GTX, y0 = blockIdx.y * GTY;
+    gauss_profiles<T>(g, a, x0, y0, true, gx, gy);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        partials[(int64_t)q * nblk + blockIdx.x] = s;
+    const int tx = threadIdx.x % GTX, ty = threadIdx.x / GTX;
+    T acc[GRY];
+#pragma unroll
+    for (int r = 0; r < GRY; ++r) acc[r] = T(0);
+    for (int p = 0; p < a.np; ++p) {
+        const T xv = gx[p * GTX + tx];
+        const T *yr = gy + p * GTY + ty * GRY;
+#pragma unroll
+        for (int r = 0; r < GRY; ++r) acc[r] += yr[r] * xv;
+    }
+    const int i = x0 + tx;
+    if (i >= g.nx) return;
+#pragma unroll
+    for (int r = 0; r < GRY; ++r) {
+        const int j = y0 + ty * GRY + r;
+        if (j >= g.ny) break;
+        const int64_t idx = (int64_t)j * g.pitch + i;
+        jz[idx] = acc[r];
+        if (zero_xy) {
+            jx[idx] = T(0);
+            jy[idx] = T(0);
+        }
     }
 }
 
-// out[q] = sum_b partials (weights == nullptr), or acc[q] += weights[q] * sum_b partials
-__global__ void k_gauss_project_final(const double *partials, int nblk, int np, const double *weights, double *out) {
+// partials[q * nblk + b] = sum over the tiles of block b of f * G_q: products
+// and the sum over one warp's 256 cells in T, everything above in FP64
+template <typename T>
+__global__ void __launch_bounds__(256) k_gauss_project(Geo g, GaussArgs a, const T *f, double *partials, int nblk) {
+    extern __shared__ __align__(16) unsigned char gsm[];
+    double *wsum = reinterpret_cast<double *>(gsm);  // [8 warps][np]
+    T *gx = reinterpret_cast<T *>(wsum + 8 * a.np);
+    T *gy = gx + a.np * GTX;
+    const int tilesx = (g.nx + GTX - 1) / GTX, ntiles = tilesx * ((g.ny + GTY - 1) / GTY);
+    const int tx = threadIdx.x % GTX, ty = threadIdx.x / GTX, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = threadIdx.x; q < 8 * a.np; q += blockDim.x) wsum[q] = 0.0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += nblk) {
+        const int x0 = (tile % tilesx) * GTX, y0 = (tile / tilesx) * GTY;
+        __syncthreads();  // previous tile's profiles are consumed
+        gauss_profiles<T>(g, a, x0, y0, false, gx, gy);
+        __syncthreads();
+        const int i = x0 + tx;
+        T fv[GRY];
+#pragma unroll
+        for (int r = 0; r < GRY; ++r) {
+            const int j = y0 + ty * GRY + r;
+            fv[r] = (i < g.nx && j < g.ny) ? f[(int64_t)j * g.pitch + i] : T(0);
+        }
+        for (int p = 0; p < a.np; ++p) {
+            const T *yr = gy + p * GTY + ty * GRY;
+            T s = T(0);
+#pragma unroll
+            for (int r = 0; r < GRY; ++r) s += yr[r] * fv[r];
+            T v = s * gx[p * GTX + tx];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) wsum[warp * a.np + p] += (double)v;
+        }
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < a.np; p += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += wsum[w * a.np + p];
+        partials[(int64_t)p * nblk + blockIdx.x] = s;
+    }
+}
+
+// out[q] = sum_b partials (no weights), or acc[q] += w_q * sum_b partials with
+// w_q = weights[q] or, when weights is nullptr and phi is given,
+// w_q = sin(omega0 t + phi_q)
+__global__ void k_gauss_project_final(const double *partials, int nblk, int np, const double *weights,
+                                      const double *phi, double omega0, double t, double *out) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= np) return;
     double s = 0.0;
     for (int b = 0; b < nblk; ++b) s += partials[(int64_t)q * nblk + b];
     if (weights) out[q] += weights[q] * s;
+    else if (phi) out[q] += sin(omega0 * t + phi[q]) * s;
     else out[q] = s;
 }
 
@@ -181,18 +257,41 @@ int launch_scale_copy(const Geo &g, T sc, T *const in[3], T *const out[3], cudaS
 }
 
 template <typename T>
-int launch_gauss_source(const Geo &g, int np, const double *cxy, const double *amp, double width, T *const J[3],
-                        cudaStream_t s) {
-    k_gauss_source<T><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, np, cxy, amp, 1.0 / (2.0 * width * width), J[0], J[1],
-                                                          J[2]);
+size_t gauss_smem(int np, bool project) {
+    return (size_t)np * (GTX + GTY) * sizeof(T) + (project ? (size_t)8 * np * sizeof(double) : 0);
+}
+
+template <typename T>
+int launch_gauss_source(const Geo &g, const GaussSrc &gs, T *const J[3], bool zero_xy, cudaStream_t s) {
+    GaussArgs a{gs.cxy, gs.amp, gs.theta, gs.phi, gs.omega0, gs.t, 1.0 / (2.0 * gs.width * gs.width), gs.np};
+    const size_t sm = gauss_smem<T>(gs.np, false);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_gauss_source<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gauss_smem<T>(128, true));
+        attr = true;
+    }
+    const dim3 grid((g.nx + GTX - 1) / GTX, (g.ny + GTY - 1) / GTY);
+    k_gauss_source<T><<<grid, 256, sm, s>>>(g, a, J[0], J[1], J[2], zero_xy ? 1 : 0);
     return 1;
 }
 
 template <typename T>
-int launch_gauss_project(const Geo &g, int np, const double *cxy, double width, const T *f, double *partials,
-                         int nblk, const double *weights, double *out, cudaStream_t s) {
-    k_gauss_project<T><<<dim3(nblk, np), 256, 0, s>>>(g, np, cxy, 1.0 / (2.0 * width * width), f, partials, nblk);
-    k_gauss_project_final<<<(np + 127) / 128, 128, 0, s>>>(partials, nblk, np, weights, out);
+int launch_gauss_project(const Geo &g, const GaussSrc &gs, const T *f, double *partials, int64_t cap,
+                         const double *weights, double *out, cudaStream_t s) {
+    GaussArgs a{gs.cxy, nullptr, nullptr, nullptr, 0.0, 0.0, 1.0 / (2.0 * gs.width * gs.width), gs.np};
+    const int ntiles = ((g.nx + GTX - 1) / GTX) * ((g.ny + GTY - 1) / GTY);
+    int64_t nblk = cap / gs.np;
+    if (nblk > ntiles) nblk = ntiles;
+    if (nblk > 1024) nblk = 1024;
+    if (nblk < 1) return -1;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_gauss_project<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gauss_smem<T>(128, true));
+        attr = true;
+    }
+    k_gauss_project<T><<<(int)nblk, 256, gauss_smem<T>(gs.np, true), s>>>(g, a, f, partials, (int)nblk);
+    k_gauss_project_final<<<(gs.np + 127) / 128, 128, 0, s>>>(partials, (int)nblk, gs.np, weights, gs.phi,
+                                                               gs.omega0, gs.t, out);
     return 2;
 }
 
@@ -201,9 +300,8 @@ int launch_gauss_project(const Geo &g, int np, const double *cxy, double width, 
                                       cudaStream_t);                                                           \
     template int launch_adj_faraday<T>(const Geo &, int, const Coef<T> &, T *const[3], T *const[3], cudaStream_t); \
     template int launch_scale_copy<T>(const Geo &, T, T *const[3], T *const[3], cudaStream_t);                  \
-    template int launch_gauss_source<T>(const Geo &, int, const double *, const double *, double, T *const[3],  \
-                                        cudaStream_t);                                                         \
-    template int launch_gauss_project<T>(const Geo &, int, const double *, double, const T *, double *, int,    \
+    template int launch_gauss_source<T>(const Geo &, const GaussSrc &, T *const[3], bool, cudaStream_t);        \
+    template int launch_gauss_project<T>(const Geo &, const GaussSrc &, const T *, double *, int64_t,          \
                                          const double *, double *, cudaStream_t);
 FMX_ADJ_INST(float)
 FMX_ADJ_INST(double)

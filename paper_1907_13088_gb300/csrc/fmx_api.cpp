@@ -33,7 +33,13 @@ fmx_status cuda_fail(cudaError_t e, const char *what) {
 }
 
 constexpr size_t kAlign = 256;
-constexpr size_t kSmallDoubles = 1024;  // workspace room for small per-call parameter arrays
+constexpr size_t kSmallDoubles = 2048;  // workspace room for small per-call parameter arrays
+// small-region layout (doubles): Gaussian-source centres, amplitudes or
+// weights, projection output of single calls; centres, theta, phi of the
+// run set up by fmx_gauss_setup; the gradient accumulator
+constexpr size_t kGaussMax = 128;
+constexpr size_t kSmCxy = 0, kSmAmp = 256, kSmOut = 384, kSmRunCxy = 512, kSmTheta = 768, kSmPhi = 896,
+                 kSmAcc = 1024;
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 double dt_cfl(const fmx_params *p) {
@@ -176,6 +182,9 @@ struct fmx_grid {
     double *diag_out = nullptr;
     fmx::DevStatus *st = nullptr;
     double *small = nullptr;  // kSmallDoubles doubles of workspace
+    // Gaussian-source run (fmx_gauss_setup)
+    int gauss_np = 0;
+    double gauss_width = 0.0, gauss_omega0 = 0.0;
     // per-kernel timing (fmx_profile_enable): events of each profiled step
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;  // reused across reads
@@ -404,9 +413,10 @@ fmx_status copy_rows(fmx_grid *g, void *dst, size_t dpitch, const void *src, siz
     return FMX_OK;
 }
 
+// jmask: components of jbar to write (bit c = component c)
 template <typename T>
 fmx_status adjoint_impl(fmx_grid *g, void *const *Eb_, void *const *Bb_, void *const *jb_, void *work,
-                        size_t work_bytes) {
+                        size_t work_bytes, unsigned jmask = 7u) {
     if (g->p.iter_mode != FMX_ITER_FIXED) return fail(FMX_EUNSUPPORTED, "the adjoint covers fixed m only");
     if (g->p.filter_target == FMX_FILTER_FIELDS && g->p.filter_passes > 0)
         return fail(FMX_EUNSUPPORTED, "the adjoint does not cover field filtering");
@@ -418,7 +428,7 @@ fmx_status adjoint_impl(fmx_grid *g, void *const *Eb_, void *const *Bb_, void *c
         if (!Eb_[c] || !Bb_[c]) return fail(FMX_EINVAL, "NULL adjoint field");
         Eb[c] = (T *)Eb_[c];
         Bb[c] = (T *)Bb_[c];
-        jb[c] = jb_ ? (T *)jb_[c] : nullptr;
+        jb[c] = (jb_ && (jmask >> c & 1u)) ? (T *)jb_[c] : nullptr;
     }
     // staged layout: jf[3], tmp, dEp[3], dEa[3], dEb[3]
     char *w = (char *)work;
@@ -452,10 +462,11 @@ fmx_status adjoint_impl(fmx_grid *g, void *const *Eb_, void *const *Bb_, void *c
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (adjoint)");
     }
     g->launches += fmx::launch_adj_faraday<T>(g->geo, g->p.dims, c, wv, Bb, g->stream);
-    if (jb[0]) {
+    if (jb[0] || jb[1] || jb[2]) {
         g->launches += fmx::launch_scale_copy<T>(g->geo, -c.q, wv, jb, g->stream);
         if (g->p.filter_target == FMX_FILTER_CURRENT && g->p.filter_passes > 0)
             for (int q = 0; q < 3; ++q) {
+                if (!jb[q]) continue;
                 fmx_status s = filter_in_place<T>(g, jb[q], g->p.filter_passes);
                 if (s != FMX_OK) return s;
             }
@@ -712,46 +723,53 @@ fmx_status fmx_gauss_source(fmx_grid *g, int np, const double *cxy, const double
     if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
     if (!g->buf.J[0]) return fail(FMX_ESTATE, "no J buffers bound");
     if (g->p.dims != 2) return fail(FMX_EUNSUPPORTED, "the Gaussian source is 2D");
-    if ((size_t)np * 4 > kSmallDoubles / 2) return fail(FMX_EINVAL, "at most %zu sources", kSmallDoubles / 8);
-    cudaError_t e = cudaMemcpyAsync(g->small, cxy, sizeof(double) * 2 * np, cudaMemcpyHostToDevice, g->stream);
+    if ((size_t)np > kGaussMax) return fail(FMX_EINVAL, "at most %zu sources", kGaussMax);
+    cudaError_t e = cudaMemcpyAsync(g->small + kSmCxy, cxy, sizeof(double) * 2 * np, cudaMemcpyHostToDevice,
+                                    g->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(g->small + 2 * np, amp, sizeof(double) * np, cudaMemcpyHostToDevice, g->stream);
+        e = cudaMemcpyAsync(g->small + kSmAmp, amp, sizeof(double) * np, cudaMemcpyHostToDevice, g->stream);
     if (e != cudaSuccess) return cuda_fail(e, "source parameter upload");
+    const fmx::GaussSrc gs{np, g->small + kSmCxy, g->small + kSmAmp, nullptr, nullptr, 0.0, 0.0, width};
     if (g->p.precision == FMX_F64) {
         double *J[3] = {(double *)g->buf.J[0], (double *)g->buf.J[1], (double *)g->buf.J[2]};
-        g->launches += fmx::launch_gauss_source<double>(g->geo, np, g->small, g->small + 2 * np, width, J, g->stream);
+        g->launches += fmx::launch_gauss_source<double>(g->geo, gs, J, true, g->stream);
     } else {
         float *J[3] = {(float *)g->buf.J[0], (float *)g->buf.J[1], (float *)g->buf.J[2]};
-        g->launches += fmx::launch_gauss_source<float>(g->geo, np, g->small, g->small + 2 * np, width, J, g->stream);
+        g->launches += fmx::launch_gauss_source<float>(g->geo, gs, J, true, g->stream);
     }
     return check_launch(g, "Gaussian source launch");
 }
 
-// small-region layout: [0, 2np) centres, [2np, 3np) amplitudes or weights,
-// [3np, 4np) projection output, [kSmallDoubles/2, +np) accumulator
+// Projection of a device array f on the envelopes: into `out` (device) or,
+// with weights (device) or phases (device, weights sin(omega0 t + phi)), added
+// to the accumulator.
+static fmx_status gauss_project_dev(fmx_grid *g, const fmx::GaussSrc &gs, const void *f, const double *weights,
+                                    double *out) {
+    const int64_t cap = fmx::staged_partial_slots(g->geo) * 8;
+    const int n = g->p.precision == FMX_F64
+                      ? fmx::launch_gauss_project<double>(g->geo, gs, (const double *)f, g->partials, cap, weights,
+                                                          out, g->stream)
+                      : fmx::launch_gauss_project<float>(g->geo, gs, (const float *)f, g->partials, cap, weights, out,
+                                                         g->stream);
+    if (n < 0) return fail(FMX_EINVAL, "workspace too small for %d projections", gs.np);
+    g->launches += n;
+    return check_launch(g, "Gaussian projection launch");
+}
+
 static fmx_status gauss_project_impl(fmx_grid *g, int np, const double *cxy, double width, const void *f,
                                      const double *weights, double *out_host) {
     if (!g || !cxy || !f || np < 1 || !(width > 0.0)) return fail(FMX_EINVAL, "bad arguments");
     if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
     if (g->p.dims != 2) return fail(FMX_EUNSUPPORTED, "the Gaussian source is 2D");
-    if ((size_t)np * 4 > kSmallDoubles / 2) return fail(FMX_EINVAL, "at most %zu sources", kSmallDoubles / 8);
-    const int64_t cap = g->nparts * 8;
-    int nblk = (int)(cap / np);
-    if (nblk > 64) nblk = 64;
-    if (nblk < 1) return fail(FMX_EINVAL, "workspace too small for %d projections", np);
-    cudaError_t e = cudaMemcpyAsync(g->small, cxy, sizeof(double) * 2 * np, cudaMemcpyHostToDevice, g->stream);
+    if ((size_t)np > kGaussMax) return fail(FMX_EINVAL, "at most %zu sources", kGaussMax);
+    cudaError_t e = cudaMemcpyAsync(g->small + kSmCxy, cxy, sizeof(double) * 2 * np, cudaMemcpyHostToDevice,
+                                    g->stream);
     if (e == cudaSuccess && weights)
-        e = cudaMemcpyAsync(g->small + 2 * np, weights, sizeof(double) * np, cudaMemcpyHostToDevice, g->stream);
+        e = cudaMemcpyAsync(g->small + kSmAmp, weights, sizeof(double) * np, cudaMemcpyHostToDevice, g->stream);
     if (e != cudaSuccess) return cuda_fail(e, "projection parameter upload");
-    const double *w = weights ? g->small + 2 * np : nullptr;
-    double *dout = weights ? g->small + kSmallDoubles / 2 : g->small + 3 * np;
-    if (g->p.precision == FMX_F64)
-        g->launches += fmx::launch_gauss_project<double>(g->geo, np, g->small, width, (const double *)f, g->partials,
-                                                         nblk, w, dout, g->stream);
-    else
-        g->launches += fmx::launch_gauss_project<float>(g->geo, np, g->small, width, (const float *)f, g->partials,
-                                                        nblk, w, dout, g->stream);
-    fmx_status s = check_launch(g, "Gaussian projection launch");
+    const fmx::GaussSrc gs{np, g->small + kSmCxy, nullptr, nullptr, nullptr, 0.0, 0.0, width};
+    double *dout = weights ? g->small + kSmAcc : g->small + kSmOut;
+    fmx_status s = gauss_project_dev(g, gs, f, weights ? g->small + kSmAmp : nullptr, dout);
     if (s != FMX_OK || !out_host) return s;
     e = cudaMemcpyAsync(out_host, dout, sizeof(double) * np, cudaMemcpyDeviceToHost, g->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
@@ -764,25 +782,96 @@ fmx_status fmx_gauss_project(fmx_grid *g, int np, const double *cxy, double widt
     return gauss_project_impl(g, np, cxy, width, f, nullptr, out);
 }
 
+static fmx_status gauss_reset_acc(fmx_grid *g, int np) {
+    cudaError_t e = cudaMemsetAsync(g->small + kSmAcc, 0, sizeof(double) * np, g->stream);
+    return e == cudaSuccess ? FMX_OK : cuda_fail(e, "cudaMemsetAsync");
+}
+
 fmx_status fmx_gauss_accumulate(fmx_grid *g, int np, const double *cxy, double width, const void *f,
                                 const double *weights, int reset) {
     if (!g || !weights) return fail(FMX_EINVAL, "NULL argument");
     if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
-    if ((size_t)np * 4 > kSmallDoubles / 2) return fail(FMX_EINVAL, "at most %zu sources", kSmallDoubles / 8);
+    if (np < 1 || (size_t)np > kGaussMax) return fail(FMX_EINVAL, "1 to %zu sources", kGaussMax);
     if (reset) {
-        cudaError_t e = cudaMemsetAsync(g->small + kSmallDoubles / 2, 0, sizeof(double) * np, g->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+        fmx_status s = gauss_reset_acc(g, np);
+        if (s != FMX_OK) return s;
     }
     return gauss_project_impl(g, np, cxy, width, f, weights, nullptr);
 }
 
 fmx_status fmx_gauss_accumulated(fmx_grid *g, int np, double *out) {
-    if (!g || !out || np < 1) return fail(FMX_EINVAL, "bad arguments");
+    if (!g || !out || np < 1 || (size_t)np > kGaussMax) return fail(FMX_EINVAL, "bad arguments");
     if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
-    cudaError_t e = cudaMemcpyAsync(out, g->small + kSmallDoubles / 2, sizeof(double) * np, cudaMemcpyDeviceToHost,
-                                    g->stream);
+    cudaError_t e = cudaMemcpyAsync(out, g->small + kSmAcc, sizeof(double) * np, cudaMemcpyDeviceToHost, g->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return cuda_fail(e, "accumulator read-back");
+    return FMX_OK;
+}
+
+fmx_status fmx_gauss_setup(fmx_grid *g, int np, const double *cxy, const double *theta, const double *phi,
+                           double width, double omega0) {
+    if (!g || !cxy || !theta || !phi || !(width > 0.0) || !isfinite(omega0)) return fail(FMX_EINVAL, "bad arguments");
+    if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
+    if (g->p.dims != 2) return fail(FMX_EUNSUPPORTED, "the Gaussian source is 2D");
+    if (np < 1 || (size_t)np > kGaussMax) return fail(FMX_EINVAL, "1 to %zu sources", kGaussMax);
+    cudaError_t e = cudaMemcpyAsync(g->small + kSmRunCxy, cxy, sizeof(double) * 2 * np, cudaMemcpyHostToDevice,
+                                    g->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->small + kSmTheta, theta, sizeof(double) * np, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->small + kSmPhi, phi, sizeof(double) * np, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);  // host arrays are read before return
+    if (e != cudaSuccess) return cuda_fail(e, "source set-up upload");
+    g->gauss_np = np;
+    g->gauss_width = width;
+    g->gauss_omega0 = omega0;
+    return FMX_OK;
+}
+
+static fmx::GaussSrc gauss_run_src(const fmx_grid *g, int64_t n) {
+    return fmx::GaussSrc{g->gauss_np, g->small + kSmRunCxy, nullptr, g->small + kSmTheta, g->small + kSmPhi,
+                         g->gauss_omega0, ((double)n + 0.5) * g->dt, g->gauss_width};
+}
+
+fmx_status fmx_gauss_run(fmx_grid *g, int64_t n0, int nsteps) {
+    if (!g) return fail(FMX_EINVAL, "NULL grid");
+    if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
+    if (!g->buf.J[0]) return fail(FMX_ESTATE, "no J buffers bound");
+    if (g->gauss_np < 1) return fail(FMX_ESTATE, "fmx_gauss_setup not called");
+    if (nsteps < 0) return fail(FMX_EINVAL, "nsteps < 0");
+    for (int k = 0; k < nsteps; ++k) {
+        const fmx::GaussSrc gs = gauss_run_src(g, n0 + k);
+        if (g->p.precision == FMX_F64) {
+            double *J[3] = {(double *)g->buf.J[0], (double *)g->buf.J[1], (double *)g->buf.J[2]};
+            g->launches += fmx::launch_gauss_source<double>(g->geo, gs, J, k == 0, g->stream);
+        } else {
+            float *J[3] = {(float *)g->buf.J[0], (float *)g->buf.J[1], (float *)g->buf.J[2]};
+            g->launches += fmx::launch_gauss_source<float>(g->geo, gs, J, k == 0, g->stream);
+        }
+        fmx_status s = check_launch(g, "Gaussian source launch");
+        if (s == FMX_OK) s = fmx_step(g, 1);
+        if (s != FMX_OK) return s;
+    }
+    return FMX_OK;
+}
+
+fmx_status fmx_gauss_adjoint_run(fmx_grid *g, int64_t n0, int nsteps, void *const *Ebar, void *const *Bbar,
+                                 void *const *jbar, void *work, size_t work_bytes, int reset) {
+    if (!g || !Ebar || !Bbar || !jbar || !jbar[2]) return fail(FMX_EINVAL, "NULL argument");
+    if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
+    if (g->gauss_np < 1) return fail(FMX_ESTATE, "fmx_gauss_setup not called");
+    if (nsteps < 0) return fail(FMX_EINVAL, "nsteps < 0");
+    if (reset) {
+        fmx_status s = gauss_reset_acc(g, g->gauss_np);
+        if (s != FMX_OK) return s;
+    }
+    for (int k = nsteps - 1; k >= 0; --k) {
+        // only dL/dj_z enters the source gradient
+        fmx_status s = g->p.precision == FMX_F64 ? adjoint_impl<double>(g, Ebar, Bbar, jbar, work, work_bytes, 4u)
+                                                 : adjoint_impl<float>(g, Ebar, Bbar, jbar, work, work_bytes, 4u);
+        if (s == FMX_OK) s = gauss_project_dev(g, gauss_run_src(g, n0 + k), jbar[2], nullptr, g->small + kSmAcc);
+        if (s != FMX_OK) return s;
+    }
     return FMX_OK;
 }
 

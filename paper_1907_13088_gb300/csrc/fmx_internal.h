@@ -96,11 +96,20 @@ template <typename T>
 int launch_adj_faraday(const Geo &g, int dims, const Coef<T> &c, T *const w[3], T *const Bb[3], cudaStream_t s);
 template <typename T>
 int launch_scale_copy(const Geo &g, T sc, T *const in[3], T *const out[3], cudaStream_t s);
+// Gaussian-envelope current (device pointers into the grid's small region):
+// amplitudes a_p = amp[p], or theta[p] sin(omega0 t + phi[p]) when amp is
+// nullptr; for the projection, phi != nullptr and weights == nullptr make the
+// weights sin(omega0 t + phi[p]).
+struct GaussSrc {
+    int np;
+    const double *cxy, *amp, *theta, *phi;
+    double omega0, t, width;
+};
 template <typename T>
-int launch_gauss_source(const Geo &g, int np, const double *cxy, const double *amp, double width, T *const J[3],
-                        cudaStream_t s);
+int launch_gauss_source(const Geo &g, const GaussSrc &gs, T *const J[3], bool zero_xy, cudaStream_t s);
+// partials: scratch of cap doubles; returns the launches or -1 when cap < np
 template <typename T>
-int launch_gauss_project(const Geo &g, int np, const double *cxy, double width, const T *f, double *partials,
-                         int nblk, const double *weights, double *out, cudaStream_t s);
+int launch_gauss_project(const Geo &g, const GaussSrc &gs, const T *f, double *partials, int64_t cap,
+                         const double *weights, double *out, cudaStream_t s);
 
 }  // namespace fmx

@@ -12,6 +12,15 @@
 // row loop runs in blocks of four rows from a row index that is a multiple of
 // four.  HBM traffic per cell and step: TE reads 5 and writes 3 FP32 values,
 // TM reads 4 and writes 3 (60 bytes together).
+//
+// Shared memory only carries what a thread's neighbours read.  A row is
+// stored split: the even columns (pair.x) in one array of RP floats and the
+// odd columns (pair.y) in the next, so the neighbour values a thread needs
+// (column 2t-1 = pair t-1 odd, column 2t+2 = pair t+1 even) are unit-stride
+// 4-byte loads, one wavefront per warp and free of bank conflicts.  Where
+// neighbours read only one parity, only that half is stored.  Where registers
+// allow (TE: the filtered current, sweep inputs; TM: sweep inputs), a thread's
+// own values of a row come from registers instead of back from shared memory.
 #include <cuda_runtime.h>
 
 #include "fused2d.h"
@@ -43,10 +52,13 @@ __host__ __device__ constexpr double binom_w2(int P, int k) {
 
 enum { TE = 0, TM = 1 };
 
-// rows of input prefetch held in registers (divides 4)
+// Input prefetch: PD rows ahead into registers (divides 4).  At 3 blocks/SM
+// TE has the registers for 2 rows, TM for 4 (TM at 4 blocks/SM with 2 rows,
+// or TE with 4 rows at 2 blocks/SM, measure slower; an L2 bulk prefetch of
+// the rows further ahead measured far slower still).
 template <int POL>
 struct PolPrefetch {
-    static constexpr int PD = 2;
+    static constexpr int PD = POL == TM ? 4 : 2;
 };
 
 template <int M, int P, bool HJ>
@@ -61,35 +73,44 @@ struct PolGeom {
     static_assert(2 * M + 1 <= D0, "dE' ring too shallow");
 };
 
-// number of smem rows (each NT + 2 PADP pairs) of one polarisation kernel
-template <int POL, int M, int P, bool HJ>
-__host__ __device__ constexpr int pol_rows() {
+// Shared-memory map of one polarisation kernel, in floats.  RP = floats per
+// half row (pairs of the strip plus pads).  "full" = both halves (2 RP),
+// "half" = one parity (RP).
+template <int POL, int M, int P, bool HJ, int RP>
+struct PolSmem {
     using G = PolGeom<M, P, HJ>;
-    // TE: jy[2][2], bz[4], dp[D0][2], sw[NS][4][2], e[2]
-    // TM: jy[2], bx[4], ay[2], dp[D0], sw[NS][4], e[2]
-    return POL == TE ? ((HJ ? 4 : 0) + 4 + G::D0 * 2 + G::NS * 8 + 2)
-                     : ((HJ ? 2 : 0) + 4 + 2 + G::D0 + G::NS * 4 + 2);
-}
+    static constexpr int NC = POL == TE ? 2 : 1;                     // E components of the set
+    static constexpr int J = 0;                                      // y-filtered j: [2][NC] full
+    static constexpr int B = J + (HJ ? 2 * NC * 2 * RP : 0);         // TE: Bz, TM: Bx [4] full
+    static constexpr int AY = B + 8 * RP;                            // TM: alpha_y By [2] full
+    static constexpr int DP = AY + (POL == TM ? 4 * RP : 0);         // dE': [D0][NC] full
+    static constexpr int SW = DP + G::D0 * NC * 2 * RP;              // sweeps 1..M-1: [NS][4] slots
+    static constexpr int SWS = POL == TE ? 3 * RP : 2 * RP;          //   TE: Ex odd half + Ey full; TM: Ez full
+    static constexpr int EN = SW + G::NS * 4 * SWS;                  // E^{n+1} (TE: Ey, TM: Ez): [2] even half
+    static constexpr int TOTAL = EN + 2 * RP;
+};
 
 template <int POL, int M, int P, bool HJ, int NT>
 __global__ void __launch_bounds__(NT, 3)
     k_pol2d(Fused2dArgs<float> a, Geo g, Coef2 c, int W, int L, int nstrip) {
     using G = PolGeom<M, P, HJ>;
     constexpr int HC = G::HC, PADP = G::PADP, D0 = G::D0, NS = G::NS, TJ = G::TJ;
-    constexpr int RP = NT + 2 * PADP;  // pairs per smem row
-    constexpr int NC = POL == TE ? 2 : 1;  // E components of the set
+    constexpr int RP = NT + 2 * PADP;  // pairs (floats of a half row) per smem row
+    using S = PolSmem<POL, M, P, HJ, RP>;
+    constexpr int NC = S::NC;
+    // own values from registers (TE) or read back from smem (TM: 4 blocks/SM leave no room)
+    constexpr bool RJ = POL == TE;
     extern __shared__ __align__(16) unsigned char smraw[];
-    f2 *sm = reinterpret_cast<f2 *>(smraw);
-    f2 *s_jy = sm;                                     // [2][NC][RP]
-    f2 *s_b0 = s_jy + (HJ ? 2 * NC * RP : 0);          // [4][RP]  TE: Bz, TM: Bx
-    f2 *s_ay = s_b0 + 4 * RP;                          // [2][RP]  TM only: alpha_y By
-    f2 *s_dp = s_ay + (POL == TM ? 2 * RP : 0);        // [D0][NC][RP]
-    f2 *s_sw = s_dp + D0 * NC * RP;                    // [NS][4][NC][RP]
-    f2 *s_e = s_sw + NS * 4 * NC * RP;                 // [2][RP]  TE: Ey, TM: Ez of E^{n+1}
-    constexpr int total = pol_rows<POL, M, P, HJ>() * RP;
+    float *sm = reinterpret_cast<float *>(smraw);
+    float *s_j = sm + S::J;
+    float *s_b = sm + S::B;
+    float *s_ay = sm + S::AY;
+    float *s_dp = sm + S::DP;
+    float *s_sw = sm + S::SW;
+    float *s_e = sm + S::EN;
 
     const int tid = threadIdx.x;
-    for (int q = tid; q < total; q += NT) sm[q] = mk(0.f, 0.f);
+    for (int q = tid; q < S::TOTAL; q += NT) sm[q] = 0.f;
 
     const int strip = blockIdx.x % nstrip, seg = blockIdx.x / nstrip;
     const int x0 = strip * W;
@@ -100,9 +121,14 @@ __global__ void __launch_bounds__(NT, 3)
     if (xc < 0) xc += g.nx;
     const bool xout = 2 * tid >= HC && 2 * tid < HC + W && cg < g.nx;
     const int pc = tid + PADP;  // pair index in an smem row
-    // scalar views of smem rows: column 2t-1 and 2t+2 of this thread
-    auto left = [&](const f2 *row) { return reinterpret_cast<const float *>(row)[2 * pc - 1]; };
-    auto right = [&](const f2 *row) { return reinterpret_cast<const float *>(row)[2 * pc + 2]; };
+    // full row: column 2t-1 (left), 2t+2 (right), own pair, store
+    auto lft = [&](const float *row) { return row[RP + pc - 1]; };
+    auto rgt = [&](const float *row) { return row[pc + 1]; };
+    auto own = [&](const float *row) { return mk(row[pc], row[RP + pc]); };
+    auto put = [&](float *row, f2 v) {
+        row[pc] = v.x;
+        row[RP + pc] = v.y;
+    };
 
     // inputs of the set
     const float *__restrict__ inJ0 = POL == TE ? a.J[0] : a.J[2];
@@ -137,17 +163,19 @@ __global__ void __launch_bounds__(NT, 3)
 
     // register state (pairs)
     f2 jw[NC][TJ];
+    f2 jd[NC];           // TE: y-filtered j of row r (own pair; TM reads it back from smem)
     f2 byw[3];           // TM: By rows r+2, r+1, r
     f2 bprev;            // TE: Bz row r-1   TM: alpha_x Bx row r-1
     f2 win[M > 0 ? M : 1][NC][3];
     f2 aux[M > 0 ? M : 1][3];  // TE: h = Dbar_x Ex (rows rho+1, rho)   TM: Dbar_xx Ez (rho+1, rho, rho-1)
+    float eyrp[M > 0 ? M : 1];  // TE: Ey at column 2t+2, row rho-1 of each sweep's input
     f2 en[NC], enp[NC];
     const f2 z2 = mk(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
 #pragma unroll
         for (int k = 0; k < TJ; ++k) jw[q][k] = z2;
-        en[q] = enp[q] = z2;
+        en[q] = enp[q] = jd[q] = z2;
     }
     byw[0] = byw[1] = byw[2] = z2;
     bprev = z2;
@@ -156,6 +184,7 @@ __global__ void __launch_bounds__(NT, 3)
 #pragma unroll
         for (int q = 0; q < NC; ++q) win[s][q][0] = win[s][q][1] = win[s][q][2] = z2;
         aux[s][0] = aux[s][1] = aux[s][2] = z2;
+        eyrp[s] = 0.f;
     }
 
     auto ld2 = [&](const float *p, int64_t o) { return __ldg(reinterpret_cast<const float2 *>(p + o)); };
@@ -190,6 +219,7 @@ __global__ void __launch_bounds__(NT, 3)
         adv_all();
     }
     int b0 = ((r0 % D0) + D0) % D0;  // dE' ring slot of row r0 (a multiple of 4)
+
     __syncthreads();
 
     for (int rb = r0; rb < r1; rb += 4) {
@@ -202,62 +232,117 @@ __global__ void __launch_bounds__(NT, 3)
             if (r + PD < r1) issue(k);  // row r + PD
             adv_all();
             const int rhoM = r - 2 * M, rhoF = rhoM - 1;
-            // dE' ring slot of row r - k (u, k compile-time; b0 in {0, 4, 8})
-            auto dslot = [&](int k) {
+            // dE' ring row of row r - k (u, k compile-time; b0 in {0, 4, 8})
+            auto dprow = [&](int k) {
                 int sl = b0 + u - k;
-                return sl < 0 ? sl + D0 : sl;
+                return s_dp + (sl < 0 ? sl + D0 : sl) * NC * 2 * RP;
+            };
+            // E update of row rhoM from dE_(M), Faraday update of row rhoF
+            auto finish = [&](f2 o0, f2 o1) {
+                enp[0] = en[0];
+                en[0] = add(ce0, o0);
+                if (POL == TE) {
+                    enp[1] = en[1];
+                    en[1] = add(ce1, o1);
+                }
+                const bool yE = rhoM >= y0 && rhoM < y1;
+                if (yE && xout) {
+                    const int64_t o = (int64_t)rhoM * g.pitch + xc;
+                    *reinterpret_cast<float2 *>(oE0 + o) = en[0];
+                    if (POL == TE) *reinterpret_cast<float2 *>(oE1 + o) = en[1];
+                }
+                // neighbours read column 2t+2 (even) of TE: Ey, TM: Ez
+                s_e[(u & 1) * RP + pc] = POL == TE ? en[1].x : en[0].x;
+                const float er = s_e[((u + 1) & 1) * RP + pc + 1];  // row rhoF
+                f2 bo0, bo1 = z2;
+                if constexpr (POL == TE) {
+                    // Bz -= kx (Ey[i+1] - Ey[i]) - ky (Ex[j+1] - Ex[j])
+                    const f2 dxey = fma(enp[1], c.m1, mk(enp[1].y, er));
+                    const f2 dyex = fma(enp[0], c.m1, en[0]);
+                    bo0 = fma(c.ky, dyex, fma(fma(c.kx, dxey, z2), c.m1, cf0));
+                } else {
+                    // Bx -= ky (Ez[j+1] - Ez[j]);  By += kx (Ez[i+1] - Ez[i])
+                    const f2 dyez = fma(enp[0], c.m1, en[0]);
+                    const f2 dxez = fma(enp[0], c.m1, mk(enp[0].y, er));
+                    bo0 = fma(fma(c.ky, dyez, z2), c.m1, cf0);
+                    bo1 = fma(c.kx, dxez, cf1);
+                }
+                const bool yF = rhoF >= y0 && rhoF < y1;
+                if (yF && xout) {
+                    const int64_t o = (int64_t)rhoF * g.pitch + xc;
+                    *reinterpret_cast<float2 *>(oB0 + o) = bo0;
+                    if (POL == TM) *reinterpret_cast<float2 *>(oB1 + o) = bo1;
+                }
             };
 
             // ---------------- sweeps M..1 ----------------
 #pragma unroll
             for (int s = M; s >= 1; --s) {
-                // rows of stage s-1: rho+1, rho, rho-1 (ring slots)
-                const f2 *rp1, *r0w, *rm1;
+                // input rows of sweep s (outputs of stage s-1): rho+1 and rho.
+                // TE: xo = odd half of Ex, ey = full Ey; TM: ez = full Ez.
+                const float *xo_p1, *ey_0, *ez_p1;
                 if (s == 1) {
-                    rp1 = s_dp + dslot(2 * s - 1) * NC * RP;
-                    r0w = s_dp + dslot(2 * s) * NC * RP;
-                    rm1 = s_dp + dslot(2 * s + 1) * NC * RP;
+                    const float *rp1 = dprow(2 * s - 1), *r0w = dprow(2 * s);
+                    xo_p1 = rp1 + RP;
+                    ey_0 = r0w + 2 * RP;
+                    ez_p1 = rp1;
                 } else {
-                    const f2 *base = s_sw + (s - 2) * 4 * NC * RP;
-                    rp1 = base + ((u - 2 * s + 1 + 16) & 3) * NC * RP;
-                    r0w = base + ((u - 2 * s + 16) & 3) * NC * RP;
-                    rm1 = base + ((u - 2 * s - 1 + 16) & 3) * NC * RP;
+                    const float *base = s_sw + (s - 2) * 4 * S::SWS;
+                    const float *rp1 = base + ((u - 2 * s + 1 + 16) & 3) * S::SWS;
+                    const float *r0w = base + ((u - 2 * s + 16) & 3) * S::SWS;
+                    xo_p1 = rp1;
+                    ey_0 = r0w + RP;
+                    ez_p1 = rp1;
                 }
-                const f2 *dp = s_dp + dslot(2 * s) * NC * RP;
+                // dE' of row rho (own pair): sweep 1 holds it in its window
+                f2 dp0, dp1 = z2;
+                if (s == 1) {
+                    dp0 = win[0][0][1];
+                    if (POL == TE) dp1 = win[0][1][1];
+                } else {
+                    const float *dr = dprow(2 * s);
+                    dp0 = own(dr);
+                    if (POL == TE) dp1 = own(dr + 2 * RP);
+                }
                 f2 o0, o1 = z2;
                 if constexpr (POL == TE) {
                     const f2 *X = win[s - 1][0];
                     const f2 *Y = win[s - 1][1];
                     // h = Dbar_x(bwd) Ex at row rho+1: X0 - (Ex[2t-1], X0.x)
-                    const float exl = left(rp1);
+                    const float exl = xo_p1[pc - 1];
                     aux[s - 1][1] = aux[s - 1][0];
                     aux[s - 1][0] = fma(mk(exl, X[0].x), c.m1, X[0]);
-                    const float eyl = left(r0w + RP), eyr = right(r0w + RP), eyr_m = right(rm1 + RP);
+                    const float eyl = lft(ey_0), eyr = rgt(ey_0), eyr_m = eyrp[s - 1];
+                    eyrp[s - 1] = eyr;
                     const f2 g_own = fma(Y[2], c.m1, Y[1]);
                     const f2 g_nb = mk(g_own.y, eyr - eyr_m);
                     const f2 dyyx = fma(X[1], c.m2, add(X[0], X[2]));
                     const f2 dxxy = fma(Y[1], c.m2, add(mk(eyl, Y[1].x), mk(Y[1].y, eyr)));
-                    o0 = fma(c.ay, dyyx, dp[pc]);
+                    o0 = fma(c.ay, dyyx, dp0);
                     o0 = fma(c.bxy, fma(g_own, c.m1, g_nb), o0);
-                    o1 = fma(c.ax, dxxy, dp[RP + pc]);
+                    o1 = fma(c.ax, dxxy, dp1);
                     o1 = fma(c.bxy, fma(aux[s - 1][1], c.m1, aux[s - 1][0]), o1);
                 } else {
                     const f2 *Z = win[s - 1][0];
-                    const float ezl = left(rp1), ezr = right(rp1);
+                    const float ezl = lft(ez_p1), ezr = rgt(ez_p1);
                     aux[s - 1][2] = aux[s - 1][1];
                     aux[s - 1][1] = aux[s - 1][0];
                     aux[s - 1][0] = fma(Z[0], c.m2, add(mk(ezl, Z[0].x), mk(Z[0].y, ezr)));
                     const f2 *D = aux[s - 1];
                     const f2 dyy = fma(Z[1], c.m2, add(Z[0], Z[2]));
                     const f2 dxxyy = fma(D[1], c.m2, add(D[0], D[2]));
-                    o0 = fma(c.ax, D[1], dp[pc]);
+                    o0 = fma(c.ax, D[1], dp0);
                     o0 = fma(c.ay, dyy, o0);
                     o0 = fma(c.axy, dxxyy, o0);
                 }
                 if (s < M) {
-                    f2 *o = s_sw + (s - 1) * 4 * NC * RP + ((u - 2 * s + 16) & 3) * NC * RP;
-                    o[pc] = o0;
-                    if (POL == TE) o[RP + pc] = o1;
+                    float *o = s_sw + (s - 1) * 4 * S::SWS + ((u - 2 * s + 16) & 3) * S::SWS;
+                    if (POL == TE) {
+                        o[pc] = o0.y;     // Ex: neighbours read the odd column only
+                        put(o + RP, o1);  // Ey: both
+                    } else {
+                        put(o, o0);
+                    }
 #pragma unroll
                     for (int q = 0; q < NC; ++q) {
                         win[s][q][2] = win[s][q][1];
@@ -266,42 +351,7 @@ __global__ void __launch_bounds__(NT, 3)
                     win[s][0][0] = o0;
                     if (POL == TE) win[s][1][0] = o1;
                 } else {
-                    // ---------------- E update (row rhoM) and Faraday (row rhoF) ----------------
-                    enp[0] = en[0];
-                    en[0] = add(ce0, o0);
-                    if (POL == TE) {
-                        enp[1] = en[1];
-                        en[1] = add(ce1, o1);
-                    }
-                    const bool yE = rhoM >= y0 && rhoM < y1;
-                    if (yE && xout) {
-                        const int64_t o = (int64_t)rhoM * g.pitch + xc;
-                        *reinterpret_cast<float2 *>(oE0 + o) = en[0];
-                        if (POL == TE) *reinterpret_cast<float2 *>(oE1 + o) = en[1];
-                    }
-                    f2 *se = s_e + (u & 1) * RP;
-                    se[pc] = POL == TE ? en[1] : en[0];
-                    const f2 *sf = s_e + ((u + 1) & 1) * RP;  // row rhoF
-                    const float er = right(sf);
-                    f2 bo0, bo1 = z2;
-                    if constexpr (POL == TE) {
-                        // Bz -= kx (Ey[i+1] - Ey[i]) - ky (Ex[j+1] - Ex[j])
-                        const f2 dxey = fma(enp[1], c.m1, mk(enp[1].y, er));
-                        const f2 dyex = fma(enp[0], c.m1, en[0]);
-                        bo0 = fma(c.ky, dyex, fma(fma(c.kx, dxey, z2), c.m1, cf0));
-                    } else {
-                        // Bx -= ky (Ez[j+1] - Ez[j]);  By += kx (Ez[i+1] - Ez[i])
-                        const f2 dyez = fma(enp[0], c.m1, en[0]);
-                        const f2 dxez = fma(enp[0], c.m1, mk(enp[0].y, er));
-                        bo0 = fma(fma(c.ky, dyez, z2), c.m1, cf0);
-                        bo1 = fma(c.kx, dxez, cf1);
-                    }
-                    const bool yF = rhoF >= y0 && rhoF < y1;
-                    if (yF && xout) {
-                        const int64_t o = (int64_t)rhoF * g.pitch + xc;
-                        *reinterpret_cast<float2 *>(oB0 + o) = bo0;
-                        if (POL == TM) *reinterpret_cast<float2 *>(oB1 + o) = bo1;
-                    }
+                    finish(o0, o1);
                 }
             }
 
@@ -309,22 +359,24 @@ __global__ void __launch_bounds__(NT, 3)
             {
                 f2 jf0 = z2, jf1 = z2;
                 if (HJ) {
-                    const f2 *jr = s_jy + (u & 1) * NC * RP;
+                    const float *jr = s_j + (u & 1) * NC * 2 * RP;
 #pragma unroll
                     for (int q = 0; q < NC; ++q) {
-                        const f2 *row = jr + q * RP;
-                        // aligned pairs pc-H .. pc+H cover columns 2t-P .. 2t+1+P; the
-                        // odd-shifted tap pairs are assembled from them in registers
-                        constexpr int H = (P + 1) / 2;
-                        f2 pr[2 * H + 1];
+                        const float *row = jr + q * 2 * RP;
+                        // columns 2t-P .. 2t+1+P (TE: the own pair from registers)
+                        float col[2 * P + 2];
 #pragma unroll
-                        for (int d = -H; d <= H; ++d) pr[d + H] = row[pc + d];
+                        for (int i = 0; i < 2 * P + 2; ++i) {
+                            const int off = i - P;
+                            col[i] = (off == 0 && RJ)   ? jd[q].x
+                                     : (off == 1 && RJ) ? jd[q].y
+                                     : (off & 1) == 0   ? row[pc + off / 2]
+                                                        : row[RP + pc + (off - 1) / 2];
+                        }
                         f2 acc = z2;
 #pragma unroll
                         for (int k = 0; k <= 2 * P; ++k) {
-                            const int off = k - P;  // column offset of the tap
-                            const int lo = (off - 1) / 2;  // for odd off, pair t+lo holds column 2t+off
-                            const f2 v = (off & 1) == 0 ? pr[H + off / 2] : mk(pr[H + lo].y, pr[H + lo + 1].x);
+                            const f2 v = mk(col[k], col[k + 1]);
                             acc = k == 0 ? mul(c.w[0], v) : fma(c.w[k], v, acc);
                         }
                         if (q == 0) jf0 = acc; else jf1 = acc;
@@ -332,9 +384,10 @@ __global__ void __launch_bounds__(NT, 3)
                 }
                 f2 d0, d1 = z2;
                 if constexpr (POL == TE) {
-                    const f2 *sb = s_b0 + (u & 3) * RP;
-                    const f2 bz0 = sb[pc];
-                    const float bzl = left(sb);
+                    // own Bz from shared memory: a register delay line spills at 3 blocks/SM
+                    const float *sb = s_b + (u & 3) * 2 * RP;
+                    const f2 bz0 = own(sb);
+                    const float bzl = lft(sb);
                     // dE'_x = ky (Bz[j] - Bz[j-1]) - q jx ;  dE'_y = -kx (Bz[i] - Bz[i-1]) - q jy
                     d0 = mul(c.ky, fma(bprev, c.m1, bz0));
                     d1 = mul(c.kx, fma(bz0, c.m1, mk(bzl, bz0.x)));
@@ -344,21 +397,22 @@ __global__ void __launch_bounds__(NT, 3)
                         d1 = fma(c.q, fma(jf1, c.m1, z2), d1);
                     }
                 } else {
-                    const f2 *sb = s_b0 + (u & 3) * RP;
-                    const f2 bx0 = sb[pc];
-                    const f2 axbx = fma(c.c6, fma(bx0, c.m2, add(mk(left(sb), bx0.x), mk(bx0.y, right(sb)))), bx0);
-                    const f2 *sa = s_ay + (u & 1) * RP;
-                    const f2 ay0 = sa[pc];
-                    const f2 dxay = fma(mk(left(sa), ay0.x), c.m1, ay0);
+                    const float *sb = s_b + (u & 3) * 2 * RP;
+                    const f2 bx0 = own(sb);
+                    const f2 axbx = fma(c.c6, fma(bx0, c.m2, add(mk(lft(sb), bx0.x), mk(bx0.y, rgt(sb)))), bx0);
+                    const float *sa = s_ay + (u & 1) * 2 * RP;
+                    const f2 ay0 = own(sa);
+                    const float ayl = lft(sa);
+                    const f2 dxay = fma(mk(ayl, ay0.x), c.m1, ay0);
                     // dE'_z = kx Dbar_x(alpha_y By) - ky Dbar_y(alpha_x Bx) - q jz
                     d0 = fma(c.kx, dxay, mul(fma(c.ky, fma(bprev, c.m1, axbx), z2), c.m1));
                     bprev = axbx;
                     if (HJ) d0 = fma(c.q, fma(jf0, c.m1, z2), d0);
                 }
-                f2 *dp = s_dp + dslot(0) * NC * RP;
-                dp[pc] = d0;
-                if (POL == TE) dp[RP + pc] = d1;
                 if (M > 0) {
+                    float *dr = dprow(0);
+                    put(dr, d0);
+                    if (POL == TE) put(dr + 2 * RP, d1);
 #pragma unroll
                     for (int q = 0; q < NC; ++q) {
                         win[0][q][2] = win[0][q][1];
@@ -367,46 +421,13 @@ __global__ void __launch_bounds__(NT, 3)
                     win[0][0][0] = d0;
                     if (POL == TE) win[0][1][0] = d1;
                 } else {
-                    // no sweeps: dE = dE'
-                    enp[0] = en[0];
-                    en[0] = add(ce0, d0);
-                    if (POL == TE) {
-                        enp[1] = en[1];
-                        en[1] = add(ce1, d1);
-                    }
-                    const bool yE = rhoM >= y0 && rhoM < y1;
-                    if (yE && xout) {
-                        const int64_t o = (int64_t)rhoM * g.pitch + xc;
-                        *reinterpret_cast<float2 *>(oE0 + o) = en[0];
-                        if (POL == TE) *reinterpret_cast<float2 *>(oE1 + o) = en[1];
-                    }
-                    f2 *se = s_e + (u & 1) * RP;
-                    se[pc] = POL == TE ? en[1] : en[0];
-                    const f2 *sf = s_e + ((u + 1) & 1) * RP;
-                    const float er = right(sf);
-                    f2 bo0, bo1 = z2;
-                    if constexpr (POL == TE) {
-                        const f2 dxey = fma(enp[1], c.m1, mk(enp[1].y, er));
-                        const f2 dyex = fma(enp[0], c.m1, en[0]);
-                        bo0 = fma(c.ky, dyex, fma(fma(c.kx, dxey, z2), c.m1, cf0));
-                    } else {
-                        const f2 dyez = fma(enp[0], c.m1, en[0]);
-                        const f2 dxez = fma(enp[0], c.m1, mk(enp[0].y, er));
-                        bo0 = fma(fma(c.ky, dyez, z2), c.m1, cf0);
-                        bo1 = fma(c.kx, dxez, cf1);
-                    }
-                    const bool yF = rhoF >= y0 && rhoF < y1;
-                    if (yF && xout) {
-                        const int64_t o = (int64_t)rhoF * g.pitch + xc;
-                        *reinterpret_cast<float2 *>(oB0 + o) = bo0;
-                        if (POL == TM) *reinterpret_cast<float2 *>(oB1 + o) = bo1;
-                    }
+                    finish(d0, d1);  // no sweeps: dE = dE'
                 }
             }
 
             // ---------------- current: y-binomial of row r+1 ----------------
             if (HJ) {
-                f2 *jo = s_jy + ((u + 1) & 1) * NC * RP;
+                float *jo = s_j + ((u + 1) & 1) * NC * 2 * RP;
 #pragma unroll
                 for (int q = 0; q < NC; ++q) {
 #pragma unroll
@@ -415,18 +436,20 @@ __global__ void __launch_bounds__(NT, 3)
                     f2 acc = mul(c.w[0], jw[q][0]);
 #pragma unroll
                     for (int k = 1; k < TJ; ++k) acc = fma(c.w[k], jw[q][k], acc);
-                    jo[q * RP + pc] = acc;
+                    put(jo + q * 2 * RP, acc);
+                    if (RJ) jd[q] = acc;
                 }
             }
 
             // ---------------- B prep, row r+2 ----------------
             {
-                s_b0[((u + 2) & 3) * RP + pc] = cb0;
+                put(s_b + ((u + 2) & 3) * 2 * RP, cb0);
                 if (POL == TM) {
                     byw[2] = byw[1];
                     byw[1] = byw[0];
                     byw[0] = cb1;
-                    s_ay[((u + 1) & 1) * RP + pc] = fma(c.c6, fma(byw[1], c.m2, add(byw[0], byw[2])), byw[1]);
+                    // alpha_y By of row r+1
+                    put(s_ay + ((u + 1) & 1) * 2 * RP, fma(c.c6, fma(byw[1], c.m2, add(byw[0], byw[2])), byw[1]));
                 }
             }
             __syncthreads();
@@ -439,7 +462,9 @@ __global__ void __launch_bounds__(NT, 3)
 template <int POL, int M, int P, bool HJ>
 struct PolLauncher {
     static constexpr int NT = 128;
-    static size_t smem_bytes() { return (size_t)pol_rows<POL, M, P, HJ>() * (NT + 2 * PolGeom<M, P, HJ>::PADP) * 8; }
+    static size_t smem_bytes() {
+        return (size_t)PolSmem<POL, M, P, HJ, NT + 2 * PolGeom<M, P, HJ>::PADP>::TOTAL * sizeof(float);
+    }
     static int blocks_per_sm() {
         static int b = -1;
         if (b < 0) {

@@ -95,6 +95,12 @@ def _load():
         "fmx_gauss_accumulate": (ctypes.c_int, [G, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
                                                 ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
         "fmx_gauss_accumulated": (ctypes.c_int, [G, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+        "fmx_gauss_setup": (ctypes.c_int, [G, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                           ctypes.c_double, ctypes.c_double]),
+        "fmx_gauss_run": (ctypes.c_int, [G, ctypes.c_int64, ctypes.c_int]),
+        "fmx_gauss_adjoint_run": (ctypes.c_int, [G, ctypes.c_int64, ctypes.c_int, vpp, vpp, vpp, ctypes.c_void_p,
+                                                 ctypes.c_size_t, ctypes.c_int]),
         "fmx_batch_create": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(G)]),
         "fmx_batch_workspace_bytes": (ctypes.c_size_t, [G]),
         "fmx_batch_bind": (ctypes.c_int, [G, ctypes.POINTER(fmx_buffers), ctypes.c_void_p, ctypes.c_size_t]),
@@ -144,6 +150,9 @@ fmx_gauss_source = _lib.fmx_gauss_source
 fmx_gauss_project = _lib.fmx_gauss_project
 fmx_gauss_accumulate = _lib.fmx_gauss_accumulate
 fmx_gauss_accumulated = _lib.fmx_gauss_accumulated
+fmx_gauss_setup = _lib.fmx_gauss_setup
+fmx_gauss_run = _lib.fmx_gauss_run
+fmx_gauss_adjoint_run = _lib.fmx_gauss_adjoint_run
 fmx_batch_create = _lib.fmx_batch_create
 fmx_batch_workspace_bytes = _lib.fmx_batch_workspace_bytes
 fmx_batch_bind = _lib.fmx_batch_bind

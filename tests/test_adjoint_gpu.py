@@ -78,32 +78,62 @@ def test_dot_product_identity_gpu(fmx):
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
 
 
-def test_gauss_source_and_projection(fmx):
+@pytest.mark.parametrize("shape,npz,precision,tol", [((96, 80), 8, 1, 1e-13), ((200, 150), 64, 0, 3e-6),
+                                                      ((330, 258), 128, 0, 3e-6)])
+def test_gauss_source_and_projection(fmx, shape, npz, precision, tol):
+    """Separable tiled synthesis and projection against the direct sum of
+    periodic Gaussians (ragged tiles in both axes; 128 = the source limit)."""
     import torch
-    shape = (96, 80)
-    cxy, phases, theta = synth.gauss_sources(8, shape, seed=44)
+    nx, ny = shape
+    cxy, phases, theta = synth.gauss_sources(npz, shape, seed=44)
     w = 6.0
-    ii = np.arange(96)[None, :]
-    jj = np.arange(80)[:, None]
+    ii = np.arange(nx)[None, :]
+    jj = np.arange(ny)[:, None]
     G = []
     for x, y in cxy:
-        dx = (ii - x) - 96 * np.floor((ii - x) / 96 + 0.5)
-        dy = (jj - y) - 80 * np.floor((jj - y) / 80 + 0.5)
+        dx = (ii - x) - nx * np.floor((ii - x) / nx + 0.5)
+        dy = (jj - y) - ny * np.floor((jj - y) / ny + 0.5)
         G.append(np.exp(-(dx * dx + dy * dy) / (2 * w * w)))
     G = np.array(G)
-    g = fmx.Grid(shape, precision=1, engine=1)
-    fmx.check(fmx.fmx_gauss_source(g.handle, 8, np.ascontiguousarray(cxy).ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                   theta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), w))
+    g = fmx.Grid(shape, precision=precision, engine=1)
+    dp = lambda a: np.ascontiguousarray(a).ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    fmx.check(fmx.fmx_gauss_source(g.handle, npz, dp(cxy), dp(theta), w))
     _, _, J = g.get_fields(fmx.FMX_J)
     assert np.max(np.abs(J[:2])) == 0
-    assert rel_l2(J[2, 0], np.tensordot(theta, G, 1)) < 1e-13
-    f = np.random.default_rng(45).standard_normal((80, 96))
-    ft = torch.zeros((80, 96), dtype=torch.float64, device="cuda")
-    ft[:] = torch.from_numpy(f)
-    out = np.zeros(8)
-    fmx.check(fmx.fmx_gauss_project(g.handle, 8, np.ascontiguousarray(cxy).ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                    w, ctypes.c_void_p(ft.data_ptr()), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
-    assert rel_l2(out, np.einsum("pij,ij->p", G, f)) < 1e-13
+    assert rel_l2(J[2, 0], np.tensordot(theta, G, 1)) < tol
+    f = np.random.default_rng(45).standard_normal((ny, nx))
+    esz = 8 if precision == 1 else 4
+    pitch = (nx + 16 // esz - 1) // (16 // esz) * (16 // esz)
+    ft = torch.zeros((ny, pitch), dtype=torch.float64 if precision == 1 else torch.float32, device="cuda")
+    ft[:, :nx] = torch.from_numpy(f)
+    out = np.zeros(npz)
+    fmx.check(fmx.fmx_gauss_project(g.handle, npz, dp(cxy), w, ctypes.c_void_p(ft.data_ptr()), dp(out)))
+    ref = np.einsum("pij,ij->p", G, ft[:, :nx].double().cpu().numpy())
+    assert rel_l2(out, ref) < 10 * tol
+
+
+def test_gauss_run_matches_single_calls_fp64(fmx):
+    """fmx_gauss_run (amplitudes formed on the device) against the same steps
+    made of fmx_gauss_source with host amplitudes and fmx_step."""
+    shape, N, w, om = (96, 80), 7, 6.0, 0.2
+    cxy, phases, theta = synth.gauss_sources(8, shape, seed=49)
+    E0, B0, _ = synth.random_fields(shape, seed=50)
+    dp = lambda a: np.ascontiguousarray(a, dtype=np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    res = []
+    for mode in ("run", "calls"):
+        g = fmx.Grid(shape, precision=1, m=4, filter_passes=3, courant=0.5, engine=2)
+        g.set_fields(E0, B0)
+        if mode == "run":
+            fmx.check(fmx.fmx_gauss_setup(g.handle, 8, dp(cxy), dp(theta), dp(phases), w, om))
+            fmx.check(fmx.fmx_gauss_run(g.handle, 3, N))
+        else:
+            for n in range(3, 3 + N):
+                amp = theta * np.sin(om * (n + 0.5) * g.dt + phases)
+                fmx.check(fmx.fmx_gauss_source(g.handle, 8, dp(cxy), dp(amp), w))
+                g.step(1)
+        E, B, _ = g.get_fields(fmx.FMX_E | fmx.FMX_B)
+        res.append((E, B))
+    assert rel_l2(res[0][0], res[1][0]) < 1e-13 and rel_l2(res[0][1], res[1][1]) < 1e-13
 
 
 def _oracle_gradient(shape, cxy, phases, theta, E0, B0, N, mask, width, omega0, **kw):
