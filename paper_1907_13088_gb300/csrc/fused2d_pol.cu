@@ -22,6 +22,7 @@
 // allow (TE: the filtered current, sweep inputs; TM: sweep inputs), a thread's
 // own values of a row come from registers instead of back from shared memory.
 #include <cuda_runtime.h>
+#include <math.h>
 
 #include "fused2d.h"
 
@@ -35,30 +36,51 @@ __device__ __forceinline__ f2 add(f2 a, f2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ f2 mul(f2 a, f2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ f2 fma(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
 
-// coefficient pairs (both lanes equal), kept in the kernel's parameter space
+// coefficient pairs (both lanes equal), kept in the kernel's parameter space.
+// qf = q / 4^(2p): the kernels apply the x and y binomials with their integer
+// weights C(2p, k) and fold both normalisations into the current's factor
+// (a power-of-two scaling, exact in FP32).
 struct Coef2 {
-    f2 kx, ky, q, c6, ax, ay, axy, bxy;
-    f2 m1, m2;      // (-1, -1), (-2, -2)
-    f2 w[7];        // binomial weights of the x/y filter
+    f2 kx, ky, qf, ax, ay, axy, bxy;
 };
 
-__host__ __device__ constexpr double binom_w2(int P, int k) {
-    double c = 1.0;
+// binomial coefficient C(2P, k): p passes of (1, 2, 1) along one axis
+__host__ __device__ constexpr int binom2(int P, int k) {
+    int c = 1;
     for (int i = 0; i < k; ++i) c = c * (2 * P - i) / (i + 1);
-    double d = 1.0;
-    for (int i = 0; i < P; ++i) d *= 4.0;
-    return c / d;
+    return c;
+}
+
+// compile-time pairs: -1, -2 and the 1/6 of alpha = 1 + Dbar^2 / 6 (the
+// FP32 coefficient of the scheme: 1/6 rounded once, checked on the host)
+__device__ __forceinline__ f2 m1() { return make_float2(-1.f, -1.f); }
+__device__ __forceinline__ f2 m2() { return make_float2(-2.f, -2.f); }
+__device__ __forceinline__ f2 c6() { return make_float2(1.f / 6.f, 1.f / 6.f); }
+__device__ __forceinline__ f2 cst(int v) { return make_float2((float)v, (float)v); }
+
+// unnormalised (2P+1)-tap binomial of v[0..2P] (pairs), symmetric taps folded
+template <int P>
+__device__ __forceinline__ f2 binom_taps(const f2 *v) {
+    if constexpr (P == 0) {
+        return v[0];
+    } else {
+        f2 acc = add(v[0], v[2 * P]);
+#pragma unroll
+        for (int k = 1; k < P; ++k) acc = __ffma2_rn(cst(binom2(P, k)), add(v[k], v[2 * P - k]), acc);
+        return __ffma2_rn(cst(binom2(P, P)), v[P], acc);
+    }
 }
 
 enum { TE = 0, TM = 1 };
 
-// Input prefetch: PD rows ahead into registers (divides 4).  At 3 blocks/SM
-// TE has the registers for 2 rows, TM for 4 (TM at 4 blocks/SM with 2 rows,
-// or TE with 4 rows at 2 blocks/SM, measure slower; an L2 bulk prefetch of
-// the rows further ahead measured far slower still).
+// Input prefetch into registers, rows ahead per input stream (each divides
+// 4): the current, B, E, and B again for the Faraday update (that re-read of
+// rows the CTA loaded 2m+3 rows earlier hits L2).  The depths fit the 168
+// registers of 3 blocks/SM.
 template <int POL>
 struct PolPrefetch {
-    static constexpr int PD = POL == TM ? 4 : 2;
+    static constexpr int PJ = POL == TM ? 4 : 2, PB = POL == TM ? 4 : 2, PE = POL == TM ? 4 : 2,
+                         PF = POL == TM ? 4 : 2;
 };
 
 template <int M, int P, bool HJ>
@@ -66,11 +88,9 @@ struct PolGeom {
     static constexpr int PX = (HJ && P > 1) ? P : 1;            // columns of x-reach of the source
     static constexpr int HC = ((PX + M) + 1) / 2 * 2;           // left halo, even
     static constexpr int PADP = (HJ && P > 1) ? (P + 1) / 2 : 1; // smem pad, in pairs
-    static constexpr int D0 = 12;                               // dE' ring depth (>= 2M+1, multiple of 4)
     static constexpr int NS = M > 1 ? M - 1 : 0;
     static constexpr int TJ = HJ ? 2 * P + 1 : 1;
     static constexpr int WU = TJ > 3 ? TJ : 3;
-    static_assert(2 * M + 1 <= D0, "dE' ring too shallow");
 };
 
 // Shared-memory map of one polarisation kernel, in floats.  RP = floats per
@@ -80,11 +100,15 @@ template <int POL, int M, int P, bool HJ, int RP>
 struct PolSmem {
     using G = PolGeom<M, P, HJ>;
     static constexpr int NC = POL == TE ? 2 : 1;                     // E components of the set
+    // dE' ring depth: >= 2M+1 rows, a multiple of 4 (16, with a mask for the
+    // slot wrap, measured slower in both kernels: more shared memory, less L1)
+    static constexpr int D0 = 12;
+    static_assert(2 * M + 1 <= D0 && D0 % 4 == 0, "dE' ring too shallow");
     static constexpr int J = 0;                                      // y-filtered j: [2][NC] full
     static constexpr int B = J + (HJ ? 2 * NC * 2 * RP : 0);         // TE: Bz, TM: Bx [4] full
     static constexpr int AY = B + 8 * RP;                            // TM: alpha_y By [2] full
     static constexpr int DP = AY + (POL == TM ? 4 * RP : 0);         // dE': [D0][NC] full
-    static constexpr int SW = DP + G::D0 * NC * 2 * RP;              // sweeps 1..M-1: [NS][4] slots
+    static constexpr int SW = DP + D0 * NC * 2 * RP;              // sweeps 1..M-1: [NS][4] slots
     static constexpr int SWS = POL == TE ? 3 * RP : 2 * RP;          //   TE: Ex odd half + Ey full; TM: Ez full
     static constexpr int EN = SW + G::NS * 4 * SWS;                  // E^{n+1} (TE: Ey, TM: Ez): [2] even half
     static constexpr int TOTAL = EN + 2 * RP;
@@ -94,9 +118,10 @@ template <int POL, int M, int P, bool HJ, int NT>
 __global__ void __launch_bounds__(NT, 3)
     k_pol2d(Fused2dArgs<float> a, Geo g, Coef2 c, int W, int L, int nstrip) {
     using G = PolGeom<M, P, HJ>;
-    constexpr int HC = G::HC, PADP = G::PADP, D0 = G::D0, NS = G::NS, TJ = G::TJ;
+    constexpr int HC = G::HC, PADP = G::PADP, TJ = G::TJ;
     constexpr int RP = NT + 2 * PADP;  // pairs (floats of a half row) per smem row
     using S = PolSmem<POL, M, P, HJ, RP>;
+    constexpr int D0 = S::D0;
     constexpr int NC = S::NC;
     // own values from registers (TE) or read back from smem (TM: 4 blocks/SM leave no room)
     constexpr bool RJ = POL == TE;
@@ -148,16 +173,17 @@ __global__ void __launch_bounds__(NT, 3)
     int r1 = y1 + 2 * M + 1;
     r1 += (4 - ((r1 - r0) % 4)) % 4;
 
-    // running row offsets (element index of (row, xc)) of the four input rows
-    const int64_t plane = (int64_t)g.ny * g.pitch;
+    // running row offsets (element index of (row, xc)) of the four input rows;
+    // 32-bit: the launcher requires ny * pitch < 2^31
+    const int pitch = (int)g.pitch, plane = g.ny * pitch;
     auto row_off = [&](int r) {
         int y = r % g.ny;
         if (y < 0) y += g.ny;
-        return (int64_t)y * g.pitch + xc;
+        return y * pitch + xc;
     };
-    int64_t oj = row_off(r0 + 1 + P), ob = row_off(r0 + 2), oe = row_off(r0 - 2 * M), of = row_off(r0 - 2 * M - 1);
-    auto adv = [&](int64_t &o) {
-        o += g.pitch;
+    int oj = row_off(r0 + 1 + P), ob = row_off(r0 + 2), oe = row_off(r0 - 2 * M), of = row_off(r0 - 2 * M - 1);
+    auto adv = [&](int &o) {
+        o += pitch;
         if (o >= plane) o -= plane;
     };
 
@@ -187,36 +213,58 @@ __global__ void __launch_bounds__(NT, 3)
         eyrp[s] = 0.f;
     }
 
-    auto ld2 = [&](const float *p, int64_t o) { return __ldg(reinterpret_cast<const float2 *>(p + o)); };
-    // inputs of PD rows ahead, one buffer per row modulo PD (PD divides the
-    // four-row unroll, so the buffer of a row is a compile-time constant):
+    auto ld2 = [&](const float *p, int o) { return __ldg(reinterpret_cast<const float2 *>(p + o)); };
+    // one register buffer per row modulo the stream's depth (the depths divide
+    // the four-row unroll, so the buffer of a row is a compile-time constant):
     // j (NC), B (TE: Bz; TM: Bx, By), E (NC), B again for the Faraday update
-    constexpr int PD = PolPrefetch<POL>::PD;
-    f2 pj0[PD], pj1[PD], pb0[PD], pb1[PD], pe0[PD], pe1[PD], pf0[PD], pf1[PD];
-#pragma unroll
-    for (int k = 0; k < PD; ++k) pj0[k] = pj1[k] = pb0[k] = pb1[k] = pe0[k] = pe1[k] = pf0[k] = pf1[k] = z2;
-    auto issue = [&](int k) {
+    using PF_ = PolPrefetch<POL>;
+    constexpr int PJ = PF_::PJ, PB = PF_::PB, PE = PF_::PE, PFD = PF_::PF;
+    f2 pj0[PJ], pj1[PJ], pb0[PB], pb1[PB], pe0[PE], pe1[PE], pf0[PFD], pf1[PFD];
+    auto ldJ = [&](int k) {
         if (HJ) {
             pj0[k] = ld2(inJ0, oj);
             if (POL == TE) pj1[k] = ld2(inJ1, oj);
         }
+        adv(oj);
+    };
+    auto ldB = [&](int k) {
         pb0[k] = ld2(inB0, ob);
         if (POL == TM) pb1[k] = ld2(inB1, ob);
+        adv(ob);
+    };
+    auto ldE = [&](int k) {
         pe0[k] = ld2(inE0, oe);
         if (POL == TE) pe1[k] = ld2(inE1, oe);
+        adv(oe);
+    };
+    auto ldF = [&](int k) {
         pf0[k] = ld2(inB0, of);
         if (POL == TM) pf1[k] = ld2(inB1, of);
-    };
-    auto adv_all = [&]() {
-        adv(oj);
-        adv(ob);
-        adv(oe);
         adv(of);
     };
+    // rows r0 .. r0 + depth - 1 of each stream (r0 is a multiple of 4)
 #pragma unroll
-    for (int k = 0; k < PD; ++k) {  // rows r0 .. r0 + PD - 1 (r0 is a multiple of 4)
-        issue(k);
-        adv_all();
+    for (int k = 0; k < PJ; ++k) ldJ(k);
+#pragma unroll
+    for (int k = 0; k < PB; ++k) ldB(k);
+#pragma unroll
+    for (int k = 0; k < PE; ++k) ldE(k);
+#pragma unroll
+    for (int k = 0; k < PFD; ++k) ldF(k);
+    if (!HJ) {
+#pragma unroll
+        for (int k = 0; k < PJ; ++k) pj0[k] = pj1[k] = z2;
+    }
+    if (POL == TE) {
+#pragma unroll
+        for (int k = 0; k < PB; ++k) pb1[k] = z2;
+#pragma unroll
+        for (int k = 0; k < PFD; ++k) pf1[k] = z2;
+    } else {
+#pragma unroll
+        for (int k = 0; k < PJ; ++k) pj1[k] = z2;
+#pragma unroll
+        for (int k = 0; k < PE; ++k) pe1[k] = z2;
     }
     int b0 = ((r0 % D0) + D0) % D0;  // dE' ring slot of row r0 (a multiple of 4)
 
@@ -226,16 +274,21 @@ __global__ void __launch_bounds__(NT, 3)
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int r = rb + u;
-            const int k = u % PD;  // buffer of row r (compile-time)
-            const f2 cj0 = pj0[k], cj1 = pj1[k], cb0 = pb0[k], cb1 = pb1[k], ce0 = pe0[k], ce1 = pe1[k],
-                     cf0 = pf0[k], cf1 = pf1[k];
-            if (r + PD < r1) issue(k);  // row r + PD
-            adv_all();
+            // this row's inputs, then the loads of the rows `depth` ahead into
+            // the freed buffers (past the segment: valid wrapped rows, unused)
+            const f2 cj0 = pj0[u % PJ], cj1 = pj1[u % PJ], cb0 = pb0[u % PB], cb1 = pb1[u % PB],
+                     ce0 = pe0[u % PE], ce1 = pe1[u % PE], cf0 = pf0[u % PFD], cf1 = pf1[u % PFD];
+            ldJ(u % PJ);
+            ldB(u % PB);
+            ldE(u % PE);
+            ldF(u % PFD);
             const int rhoM = r - 2 * M, rhoF = rhoM - 1;
-            // dE' ring row of row r - k (u, k compile-time; b0 in {0, 4, 8})
+            // dE' ring row of row r - k (u, k compile-time; b0 a multiple of 4)
             auto dprow = [&](int k) {
                 int sl = b0 + u - k;
-                return s_dp + (sl < 0 ? sl + D0 : sl) * NC * 2 * RP;
+                if constexpr ((D0 & (D0 - 1)) == 0) sl &= D0 - 1;
+                else sl = sl < 0 ? sl + D0 : sl;
+                return s_dp + sl * NC * 2 * RP;
             };
             // E update of row rhoM from dE_(M), Faraday update of row rhoF
             auto finish = [&](f2 o0, f2 o1) {
@@ -247,7 +300,7 @@ __global__ void __launch_bounds__(NT, 3)
                 }
                 const bool yE = rhoM >= y0 && rhoM < y1;
                 if (yE && xout) {
-                    const int64_t o = (int64_t)rhoM * g.pitch + xc;
+                    const int o = rhoM * pitch + xc;
                     *reinterpret_cast<float2 *>(oE0 + o) = en[0];
                     if (POL == TE) *reinterpret_cast<float2 *>(oE1 + o) = en[1];
                 }
@@ -257,19 +310,19 @@ __global__ void __launch_bounds__(NT, 3)
                 f2 bo0, bo1 = z2;
                 if constexpr (POL == TE) {
                     // Bz -= kx (Ey[i+1] - Ey[i]) - ky (Ex[j+1] - Ex[j])
-                    const f2 dxey = fma(enp[1], c.m1, mk(enp[1].y, er));
-                    const f2 dyex = fma(enp[0], c.m1, en[0]);
-                    bo0 = fma(c.ky, dyex, fma(fma(c.kx, dxey, z2), c.m1, cf0));
+                    const f2 dxey = fma(enp[1], m1(), mk(enp[1].y, er));
+                    const f2 dyex = fma(enp[0], m1(), en[0]);
+                    bo0 = fma(c.ky, dyex, fma(fma(c.kx, dxey, z2), m1(), cf0));
                 } else {
                     // Bx -= ky (Ez[j+1] - Ez[j]);  By += kx (Ez[i+1] - Ez[i])
-                    const f2 dyez = fma(enp[0], c.m1, en[0]);
-                    const f2 dxez = fma(enp[0], c.m1, mk(enp[0].y, er));
-                    bo0 = fma(fma(c.ky, dyez, z2), c.m1, cf0);
+                    const f2 dyez = fma(enp[0], m1(), en[0]);
+                    const f2 dxez = fma(enp[0], m1(), mk(enp[0].y, er));
+                    bo0 = fma(fma(c.ky, dyez, z2), m1(), cf0);
                     bo1 = fma(c.kx, dxez, cf1);
                 }
                 const bool yF = rhoF >= y0 && rhoF < y1;
                 if (yF && xout) {
-                    const int64_t o = (int64_t)rhoF * g.pitch + xc;
+                    const int o = rhoF * pitch + xc;
                     *reinterpret_cast<float2 *>(oB0 + o) = bo0;
                     if (POL == TM) *reinterpret_cast<float2 *>(oB1 + o) = bo1;
                 }
@@ -311,26 +364,26 @@ __global__ void __launch_bounds__(NT, 3)
                     // h = Dbar_x(bwd) Ex at row rho+1: X0 - (Ex[2t-1], X0.x)
                     const float exl = xo_p1[pc - 1];
                     aux[s - 1][1] = aux[s - 1][0];
-                    aux[s - 1][0] = fma(mk(exl, X[0].x), c.m1, X[0]);
+                    aux[s - 1][0] = fma(mk(exl, X[0].x), m1(), X[0]);
                     const float eyl = lft(ey_0), eyr = rgt(ey_0), eyr_m = eyrp[s - 1];
                     eyrp[s - 1] = eyr;
-                    const f2 g_own = fma(Y[2], c.m1, Y[1]);
+                    const f2 g_own = fma(Y[2], m1(), Y[1]);
                     const f2 g_nb = mk(g_own.y, eyr - eyr_m);
-                    const f2 dyyx = fma(X[1], c.m2, add(X[0], X[2]));
-                    const f2 dxxy = fma(Y[1], c.m2, add(mk(eyl, Y[1].x), mk(Y[1].y, eyr)));
+                    const f2 dyyx = fma(X[1], m2(), add(X[0], X[2]));
+                    const f2 dxxy = fma(Y[1], m2(), add(mk(eyl, Y[1].x), mk(Y[1].y, eyr)));
                     o0 = fma(c.ay, dyyx, dp0);
-                    o0 = fma(c.bxy, fma(g_own, c.m1, g_nb), o0);
+                    o0 = fma(c.bxy, fma(g_own, m1(), g_nb), o0);
                     o1 = fma(c.ax, dxxy, dp1);
-                    o1 = fma(c.bxy, fma(aux[s - 1][1], c.m1, aux[s - 1][0]), o1);
+                    o1 = fma(c.bxy, fma(aux[s - 1][1], m1(), aux[s - 1][0]), o1);
                 } else {
                     const f2 *Z = win[s - 1][0];
                     const float ezl = lft(ez_p1), ezr = rgt(ez_p1);
                     aux[s - 1][2] = aux[s - 1][1];
                     aux[s - 1][1] = aux[s - 1][0];
-                    aux[s - 1][0] = fma(Z[0], c.m2, add(mk(ezl, Z[0].x), mk(Z[0].y, ezr)));
+                    aux[s - 1][0] = fma(Z[0], m2(), add(mk(ezl, Z[0].x), mk(Z[0].y, ezr)));
                     const f2 *D = aux[s - 1];
-                    const f2 dyy = fma(Z[1], c.m2, add(Z[0], Z[2]));
-                    const f2 dxxyy = fma(D[1], c.m2, add(D[0], D[2]));
+                    const f2 dyy = fma(Z[1], m2(), add(Z[0], Z[2]));
+                    const f2 dxxyy = fma(D[1], m2(), add(D[0], D[2]));
                     o0 = fma(c.ax, D[1], dp0);
                     o0 = fma(c.ay, dyy, o0);
                     o0 = fma(c.axy, dxxyy, o0);
@@ -373,12 +426,10 @@ __global__ void __launch_bounds__(NT, 3)
                                      : (off & 1) == 0   ? row[pc + off / 2]
                                                         : row[RP + pc + (off - 1) / 2];
                         }
-                        f2 acc = z2;
+                        f2 taps[2 * P + 1];
 #pragma unroll
-                        for (int k = 0; k <= 2 * P; ++k) {
-                            const f2 v = mk(col[k], col[k + 1]);
-                            acc = k == 0 ? mul(c.w[0], v) : fma(c.w[k], v, acc);
-                        }
+                        for (int k = 0; k <= 2 * P; ++k) taps[k] = mk(col[k], col[k + 1]);
+                        const f2 acc = binom_taps<P>(taps);
                         if (q == 0) jf0 = acc; else jf1 = acc;
                     }
                 }
@@ -389,25 +440,25 @@ __global__ void __launch_bounds__(NT, 3)
                     const f2 bz0 = own(sb);
                     const float bzl = lft(sb);
                     // dE'_x = ky (Bz[j] - Bz[j-1]) - q jx ;  dE'_y = -kx (Bz[i] - Bz[i-1]) - q jy
-                    d0 = mul(c.ky, fma(bprev, c.m1, bz0));
-                    d1 = mul(c.kx, fma(bz0, c.m1, mk(bzl, bz0.x)));
+                    d0 = mul(c.ky, fma(bprev, m1(), bz0));
+                    d1 = mul(c.kx, fma(bz0, m1(), mk(bzl, bz0.x)));
                     bprev = bz0;
                     if (HJ) {
-                        d0 = fma(c.q, fma(jf0, c.m1, z2), d0);
-                        d1 = fma(c.q, fma(jf1, c.m1, z2), d1);
+                        d0 = fma(c.qf, fma(jf0, m1(), z2), d0);
+                        d1 = fma(c.qf, fma(jf1, m1(), z2), d1);
                     }
                 } else {
                     const float *sb = s_b + (u & 3) * 2 * RP;
                     const f2 bx0 = own(sb);
-                    const f2 axbx = fma(c.c6, fma(bx0, c.m2, add(mk(lft(sb), bx0.x), mk(bx0.y, rgt(sb)))), bx0);
+                    const f2 axbx = fma(c6(), fma(bx0, m2(), add(mk(lft(sb), bx0.x), mk(bx0.y, rgt(sb)))), bx0);
                     const float *sa = s_ay + (u & 1) * 2 * RP;
                     const f2 ay0 = own(sa);
                     const float ayl = lft(sa);
-                    const f2 dxay = fma(mk(ayl, ay0.x), c.m1, ay0);
+                    const f2 dxay = fma(mk(ayl, ay0.x), m1(), ay0);
                     // dE'_z = kx Dbar_x(alpha_y By) - ky Dbar_y(alpha_x Bx) - q jz
-                    d0 = fma(c.kx, dxay, mul(fma(c.ky, fma(bprev, c.m1, axbx), z2), c.m1));
+                    d0 = fma(c.kx, dxay, mul(fma(c.ky, fma(bprev, m1(), axbx), z2), m1()));
                     bprev = axbx;
-                    if (HJ) d0 = fma(c.q, fma(jf0, c.m1, z2), d0);
+                    if (HJ) d0 = fma(c.qf, fma(jf0, m1(), z2), d0);
                 }
                 if (M > 0) {
                     float *dr = dprow(0);
@@ -433,9 +484,7 @@ __global__ void __launch_bounds__(NT, 3)
 #pragma unroll
                     for (int k = TJ - 1; k > 0; --k) jw[q][k] = jw[q][k - 1];
                     jw[q][0] = q == 0 ? cj0 : cj1;
-                    f2 acc = mul(c.w[0], jw[q][0]);
-#pragma unroll
-                    for (int k = 1; k < TJ; ++k) acc = fma(c.w[k], jw[q][k], acc);
+                    const f2 acc = binom_taps<P>(jw[q]);
                     put(jo + q * 2 * RP, acc);
                     if (RJ) jd[q] = acc;
                 }
@@ -449,7 +498,7 @@ __global__ void __launch_bounds__(NT, 3)
                     byw[1] = byw[0];
                     byw[0] = cb1;
                     // alpha_y By of row r+1
-                    put(s_ay + ((u + 1) & 1) * 2 * RP, fma(c.c6, fma(byw[1], c.m2, add(byw[0], byw[2])), byw[1]));
+                    put(s_ay + ((u + 1) & 1) * 2 * RP, fma(c6(), fma(byw[1], m2(), add(byw[0], byw[2])), byw[1]));
                 }
             }
             __syncthreads();
@@ -551,26 +600,25 @@ Coef2 make_coef2(const Coef<float> &c, int passes) {
     Coef2 k;
     k.kx = b(c.kx);
     k.ky = b(c.ky);
-    k.q = b(c.q);
-    k.c6 = b(c.c6);
+    k.qf = b(ldexpf(c.q, -4 * passes));  // q / 4^(2p), exact
     k.ax = b(c.ax);
     k.ay = b(c.ay);
     k.axy = b(c.axy);
     k.bxy = b(c.bxy);
-    k.m1 = b(-1.f);
-    k.m2 = b(-2.f);
-    for (int i = 0; i < 7; ++i) k.w[i] = b(i <= 2 * passes ? (float)binom_w2(passes, i) : 0.f);
     return k;
 }
 
 }  // namespace
 
-bool fused2d_pol_supported(const Geo &g) { return g.nx % 2 == 0; }
+// even nx (column pairs never straddle the periodic seam); 32-bit element
+// offsets within one component
+bool fused2d_pol_supported(const Geo &g) { return g.nx % 2 == 0 && (int64_t)g.ny * g.pitch < ((int64_t)1 << 31); }
 
 int launch_fused2d_pol(const Geo &g, const Coef<float> &c, const Fused2dArgs<float> &a, cudaStream_t s,
                        cudaEvent_t *ev) {
     const bool hj = a.J[0] != nullptr;
     const int p = hj ? a.passes : 0;
+    if (c.c6 != 1.f / 6.f) return -1;  // the kernels use 1/6 as a compile-time constant
     t_ev = ev;
     const int n = pol_dispatch(g, make_coef2(c, p), a, s, a.m, hj, p, nullptr);
     t_ev = nullptr;
