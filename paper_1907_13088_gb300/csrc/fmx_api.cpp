@@ -364,7 +364,7 @@ fmx_status fused_step(fmx_grid *g, int nsteps) {
     const fmx::Coef<T> c = make_coef<T>(g->co);
     for (int n = 0; n < nsteps; ++n) {
         const int nxt = 1 - g->cur;
-        fmx::Fused2dArgs<T> a;
+        fmx::Fused2dArgs<T> a{};
         for (int q = 0; q < 3; ++q) {
             a.E[q] = (const T *)g->buf.E[g->cur][q];
             a.B[q] = (const T *)g->buf.B[g->cur][q];

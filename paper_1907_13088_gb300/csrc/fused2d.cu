@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(NT, 2)
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const BatchItem w = items[it];
         const BatchGrid &G = grids[w.grid];
-        Fused2dArgs<float> a;
+        Fused2dArgs<float> a{};
         for (int q = 0; q < 3; ++q) {
             a.E[q] = G.E[parity][q];
             a.B[q] = G.B[parity][q];
