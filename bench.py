@@ -376,7 +376,10 @@ def run_adjoint(args):
                          precision=fmx.FMX_F32, checkpoint_every=50)
     FieldRun = make_function()
     th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
-    run.forward(theta, e0, b0)  # warm-up
+    # warm-up: one full forward + adjoint pass (first launches load the kernels)
+    EN, BN = FieldRun.apply(th, e0, b0, run, False)
+    (0.5 * ((EN * EN * mask).sum() + (BN * BN * mask).sum())).backward()
+    th.grad = None
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     run.forward(theta, e0, b0)
@@ -391,7 +394,7 @@ def run_adjoint(args):
     cells = shape[0] * shape[1]
     line = {
         "metric": METRIC, "value": round(cells * N / t_both / 1e9, 4), "unit": UNIT, "n_gpus": 1, "steps": N,
-        "warmup": 1, "ms_per_step": round(t_both / N * 1e3, 4), "higher_is_better": True, "scaling": "weak",
+        "warmup": N, "ms_per_step": round(t_both / N * 1e3, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "differentiable 2D 1024x1024 FP32, 64 Gaussian-envelope sources, loss = window "
                                "energy [448,576)^2 at the final step, forward + adjoint, checkpoint every 50",

@@ -112,11 +112,17 @@ struct GaussArgs {
     int np;
 };
 
-// shared layout: gx[np][GTX], gy[np][GTY] (gy pre-scaled by a_p in the source)
+// shared layout: gx[np][GTX], gy[np][GTY] (gy pre-scaled by a_p in the source);
+// amp: np doubles of shared memory for the amplitudes (source only)
 template <typename T>
 __device__ __forceinline__ void gauss_profiles(const Geo &g, const GaussArgs &a, int x0, int y0, bool scale, T *gx,
-                                               T *gy) {
+                                               T *gy, double *amp) {
     const T nx = (T)g.nx, ny = (T)g.ny, k = (T)a.inv2w2;
+    if (scale) {  // one amplitude per source (an FP64 sin each), then the profiles
+        for (int p = threadIdx.x; p < a.np; p += blockDim.x)
+            amp[p] = a.amp ? a.amp[p] : a.theta[p] * sin(a.omega0 * a.t + a.phi[p]);
+        __syncthreads();
+    }
     for (int q = threadIdx.x; q < a.np * GTX; q += blockDim.x) {
         const int p = q / GTX, i = x0 + q % GTX;
         const T dx = pdist<T>((T)i - (T)a.cxy[2 * p], nx);
@@ -126,10 +132,7 @@ __device__ __forceinline__ void gauss_profiles(const Geo &g, const GaussArgs &a,
         const int p = q / GTY, j = y0 + q % GTY;
         const T dy = pdist<T>((T)j - (T)a.cxy[2 * p + 1], ny);
         T v = gexp<T>(-dy * dy * k);
-        if (scale) {
-            const double amp = a.amp ? a.amp[p] : a.theta[p] * sin(a.omega0 * a.t + a.phi[p]);
-            v *= (T)amp;
-        }
+        if (scale) v *= (T)amp[p];
         gy[q] = v;
     }
 }
@@ -137,10 +140,11 @@ __device__ __forceinline__ void gauss_profiles(const Geo &g, const GaussArgs &a,
 template <typename T>
 __global__ void __launch_bounds__(256) k_gauss_source(Geo g, GaussArgs a, T *jx, T *jy, T *jz, int zero_xy) {
     extern __shared__ __align__(16) unsigned char gsm[];
-    T *gx = reinterpret_cast<T *>(gsm);
+    double *amp = reinterpret_cast<double *>(gsm);  // [np]
+    T *gx = reinterpret_cast<T *>(amp + a.np);
     T *gy = gx + a.np * GTX;
     const int x0 = blockIdx.x * GTX, y0 = blockIdx.y * GTY;
-    gauss_profiles<T>(g, a, x0, y0, true, gx, gy);
+    gauss_profiles<T>(g, a, x0, y0, true, gx, gy, amp);
     __syncthreads();
     const int tx = threadIdx.x % GTX, ty = threadIdx.x / GTX;
     T acc[GRY];
@@ -181,7 +185,7 @@ __global__ void __launch_bounds__(256) k_gauss_project(Geo g, GaussArgs a, const
     for (int tile = blockIdx.x; tile < ntiles; tile += nblk) {
         const int x0 = (tile % tilesx) * GTX, y0 = (tile / tilesx) * GTY;
         __syncthreads();  // previous tile's profiles are consumed
-        gauss_profiles<T>(g, a, x0, y0, false, gx, gy);
+        gauss_profiles<T>(g, a, x0, y0, false, gx, gy, nullptr);
         __syncthreads();
         const int i = x0 + tx;
         T fv[GRY];
@@ -211,13 +215,21 @@ __global__ void __launch_bounds__(256) k_gauss_project(Geo g, GaussArgs a, const
 
 // out[q] = sum_b partials (no weights), or acc[q] += w_q * sum_b partials with
 // w_q = weights[q] or, when weights is nullptr and phi is given,
-// w_q = sin(omega0 t + phi_q)
-__global__ void k_gauss_project_final(const double *partials, int nblk, int np, const double *weights,
-                                      const double *phi, double omega0, double t, double *out) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= np) return;
+// w_q = sin(omega0 t + phi_q).  One block per q; fixed summation order.
+constexpr int GFT = 128;
+__global__ void __launch_bounds__(GFT) k_gauss_project_final(const double *partials, int nblk, int np,
+                                                             const double *weights, const double *phi, double omega0,
+                                                             double t, double *out) {
+    const int q = blockIdx.x;
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += partials[(int64_t)q * nblk + b];
+    for (int b = threadIdx.x; b < nblk; b += GFT) s += partials[(int64_t)q * nblk + b];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    __shared__ double red[GFT / 32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    s = 0.0;
+    for (int w = 0; w < GFT / 32; ++w) s += red[w];
     if (weights) out[q] += weights[q] * s;
     else if (phi) out[q] += sin(omega0 * t + phi[q]) * s;
     else out[q] = s;
@@ -256,9 +268,11 @@ int launch_scale_copy(const Geo &g, T sc, T *const in[3], T *const out[3], cudaS
     return 1;
 }
 
+// the source adds np doubles for the amplitudes, the projection 8 np for the
+// per-warp sums (both in front of the profiles, so these stay 8-byte aligned)
 template <typename T>
 size_t gauss_smem(int np, bool project) {
-    return (size_t)np * (GTX + GTY) * sizeof(T) + (project ? (size_t)8 * np * sizeof(double) : 0);
+    return (size_t)np * (GTX + GTY) * sizeof(T) + (size_t)(project ? 8 : 1) * np * sizeof(double);
 }
 
 template <typename T>
@@ -290,8 +304,7 @@ int launch_gauss_project(const Geo &g, const GaussSrc &gs, const T *f, double *p
         attr = true;
     }
     k_gauss_project<T><<<(int)nblk, 256, gauss_smem<T>(gs.np, true), s>>>(g, a, f, partials, (int)nblk);
-    k_gauss_project_final<<<(gs.np + 127) / 128, 128, 0, s>>>(partials, (int)nblk, gs.np, weights, gs.phi,
-                                                               gs.omega0, gs.t, out);
+    k_gauss_project_final<<<gs.np, GFT, 0, s>>>(partials, (int)nblk, gs.np, weights, gs.phi, gs.omega0, gs.t, out);
     return 2;
 }
 

@@ -377,7 +377,8 @@ fmx_status fused_step(fmx_grid *g, int nsteps) {
         cudaEvent_t *ev = g->prof ? profile_events(g, 3) : nullptr;
         int nl;
         if constexpr (sizeof(T) == 4) {
-            if (fmx::fused2d_pol_supported(g->geo)) {
+            // the TE/TM kernels take alpha's 1/6 as a compile-time constant (lumped mode zeroes it)
+            if (fmx::fused2d_pol_supported(g->geo) && c.c6 == 1.f / 6.f) {
                 nl = fmx::launch_fused2d_pol(g->geo, c, a, g->stream, ev);
                 g->prof_kinds = 2;
             } else {
@@ -413,6 +414,55 @@ fmx_status copy_rows(fmx_grid *g, void *dst, size_t dpitch, const void *src, siz
     return FMX_OK;
 }
 
+// Whether the fused FP32 2D adjoint kernels cover the grid (grids stepped by
+// the fused engine; the staged engine's grids keep the staged adjoint), and
+// the filter passes they apply to jbar.
+bool adjoint_fused_ok(const fmx_grid *g, int *passes) {
+    *passes = g->p.filter_target == FMX_FILTER_CURRENT ? g->p.filter_passes : 0;
+    return g->p.precision == FMX_F32 && g->p.dims == 2 && g->engine == FMX_ENGINE_FUSED &&
+           g->p.iter_mode == FMX_ITER_FIXED && !(g->p.filter_target == FMX_FILTER_FIELDS && g->p.filter_passes > 0) &&
+           (float)g->co[4] == 1.f / 6.f && fmx::adjoint2d_supported(g->geo, g->p.m, *passes);
+}
+
+// One fused adjoint step from (Eb, Bb) into (Ebo, Bbo) (out of place), jbar
+// components whose pointer is set.
+fmx_status adjoint_fused(fmx_grid *g, float *const Eb[3], float *const Bb[3], float *const Ebo[3],
+                         float *const Bbo[3], float *const jb[3], int passes) {
+    fmx::Adj2dArgs<float> a{};
+    for (int q = 0; q < 3; ++q) {
+        a.Eb[q] = Eb[q];
+        a.Bb[q] = Bb[q];
+        a.Ebo[q] = Ebo[q];
+        a.Bbo[q] = Bbo[q];
+        a.Jbo[q] = jb[q];
+    }
+    a.m = g->p.m;
+    a.passes = passes;
+    const int n = fmx::launch_adjoint2d(g->geo, make_coef<float>(g->co), a, g->stream);
+    if (n < 0) return fail(FMX_EUNSUPPORTED, "fused 2D adjoint: configuration not instantiated");
+    g->launches += n;
+    return check_launch(g, "fused adjoint launch");
+}
+
+// the workspace arrays the fused adjoint writes into (the staged layout's
+// dEa and dEb: jf[3], tmp, dEp[3], dEa[3], dEb[3])
+void adjoint_scratch(const fmx_grid *g, void *work, float *Ebo[3], float *Bbo[3]) {
+    char *w = (char *)work;
+    const size_t fb = align_up(g->field_bytes, kAlign);
+    for (int c = 0; c < 3; ++c) {
+        Ebo[c] = (float *)(w + (7 + c) * fb);
+        Bbo[c] = (float *)(w + (10 + c) * fb);
+    }
+}
+
+fmx_status copy_back(fmx_grid *g, float *const dst[6], float *const src[6]) {
+    for (int q = 0; q < 6; ++q) {
+        cudaError_t e = cudaMemcpyAsync(dst[q], src[q], g->field_bytes, cudaMemcpyDeviceToDevice, g->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (adjoint)");
+    }
+    return FMX_OK;
+}
+
 // jmask: components of jbar to write (bit c = component c)
 template <typename T>
 fmx_status adjoint_impl(fmx_grid *g, void *const *Eb_, void *const *Bb_, void *const *jb_, void *work,
@@ -429,6 +479,18 @@ fmx_status adjoint_impl(fmx_grid *g, void *const *Eb_, void *const *Bb_, void *c
         Eb[c] = (T *)Eb_[c];
         Bb[c] = (T *)Bb_[c];
         jb[c] = (jb_ && (jmask >> c & 1u)) ? (T *)jb_[c] : nullptr;
+    }
+    if constexpr (sizeof(T) == 4) {
+        int passes;
+        if (adjoint_fused_ok(g, &passes)) {
+            float *Eo[3], *Bo[3];
+            adjoint_scratch(g, work, Eo, Bo);
+            fmx_status s = adjoint_fused(g, Eb, Bb, Eo, Bo, jb, passes);
+            if (s != FMX_OK) return s;
+            float *dst[6] = {Eb[0], Eb[1], Eb[2], Bb[0], Bb[1], Bb[2]};
+            float *src[6] = {Eo[0], Eo[1], Eo[2], Bo[0], Bo[1], Bo[2]};
+            return copy_back(g, dst, src);
+        }
     }
     // staged layout: jf[3], tmp, dEp[3], dEa[3], dEb[3]
     char *w = (char *)work;
@@ -864,6 +926,30 @@ fmx_status fmx_gauss_adjoint_run(fmx_grid *g, int64_t n0, int nsteps, void *cons
     if (reset) {
         fmx_status s = gauss_reset_acc(g, g->gauss_np);
         if (s != FMX_OK) return s;
+    }
+    int passes;
+    if (adjoint_fused_ok(g, &passes)) {
+        // fused adjoint, ping-pong between the caller's arrays and the
+        // workspace; one copy back at the end when the result sits in the latter
+        const size_t need = workspace_of(&g->p, FMX_ENGINE_STAGED);
+        if (!work || work_bytes < need) return fail(FMX_EINVAL, "adjoint workspace of %zu bytes needed", need);
+        if ((uintptr_t)work % kAlign) return fail(FMX_EINVAL, "adjoint workspace must be 256-byte aligned");
+        float *set[2][6];
+        for (int q = 0; q < 3; ++q) {
+            if (!Ebar[q] || !Bbar[q]) return fail(FMX_EINVAL, "NULL adjoint field");
+            set[0][q] = (float *)Ebar[q];
+            set[0][3 + q] = (float *)Bbar[q];
+        }
+        adjoint_scratch(g, work, set[1], set[1] + 3);
+        float *jz[3] = {nullptr, nullptr, (float *)jbar[2]};  // only dL/dj_z enters the source gradient
+        int cur = 0;
+        for (int k = nsteps - 1; k >= 0; --k) {
+            fmx_status s = adjoint_fused(g, set[cur], set[cur] + 3, set[1 - cur], set[1 - cur] + 3, jz, passes);
+            if (s == FMX_OK) s = gauss_project_dev(g, gauss_run_src(g, n0 + k), jbar[2], nullptr, g->small + kSmAcc);
+            if (s != FMX_OK) return s;
+            cur = 1 - cur;
+        }
+        return cur == 0 ? FMX_OK : copy_back(g, set[0], set[1]);
     }
     for (int k = nsteps - 1; k >= 0; --k) {
         // only dL/dj_z enters the source gradient

@@ -46,6 +46,27 @@ int launch_fused2d_pol(const Geo &g, const Coef<float> &c, const Fused2dArgs<flo
                        cudaEvent_t *ev = nullptr);
 Fused2dShape fused2d_pol_shape(const Geo &g, int m, int passes);
 
+// Fused 2D adjoint step (adjoint2d.cu), FP32, TE and TM kernels.  Maps
+// (Ebar, Bbar) = dL/d(E^{n+1}, B^{n+3/2}) to dL/d(E^n, B^{n+1/2}) and writes
+// dL/dj^{n+1/2} for the components whose Jbo pointer is set:
+//   u = Ebar - C_b Bbar (the source curl without averaging), Ebar' = u,
+//   w = sum_{s<=m} A^s u (the m sweeps of Algorithm 1; A is symmetric),
+//   Bbar' = Bbar + S C_f w (the Faraday curl, alpha-averaged along each B
+//   component's own axis), jbar = -4 pi dt F^p w (F symmetric).
+template <typename T>
+struct Adj2dArgs {
+    const T *Eb[3];  // dL/dE^{n+1}
+    const T *Bb[3];  // dL/dB^{n+3/2}
+    T *Ebo[3];       // dL/dE^n (must not alias Eb or Bb)
+    T *Bbo[3];       // dL/dB^{n+1/2} (must not alias Eb or Bb)
+    T *Jbo[3];       // dL/dj^{n+1/2} per component, or nullptr
+    int m;           // sweeps
+    int passes;      // binomial passes of the current filter
+};
+// even nx, 32-bit element offsets; m <= 4, passes <= 3
+bool adjoint2d_supported(const Geo &g, int m, int passes);
+int launch_adjoint2d(const Geo &g, const Coef<float> &c, const Adj2dArgs<float> &a, cudaStream_t s);
+
 // Batched step (fused2d.cu): independent FP32 grids advanced by one
 // persistent launch per step over (grid, strip, segment) tiles.
 struct BatchGrid {

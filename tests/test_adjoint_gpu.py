@@ -33,22 +33,23 @@ def _dev_pitched(a, pitch, dtype):
     return t
 
 
-def _adjoint_gpu(fmx, shape, Ebar, Bbar, **kw):
+def _adjoint_gpu(fmx, shape, Ebar, Bbar, precision=1, with_jbar=True, **kw):
     import torch
-    g = fmx.Grid(shape, precision=1, **kw)
-    esz, q = 8, 2
+    g = fmx.Grid(shape, precision=precision, **kw)
+    q = 2 if precision == 1 else 4
+    dt_ = torch.float64 if precision == 1 else torch.float32
     nx = shape[0]
     pitch = (nx + q - 1) // q * q
-    Eb = _dev_pitched(Ebar, pitch, torch.float64)
-    Bb = _dev_pitched(Bbar, pitch, torch.float64)
+    Eb = _dev_pitched(Ebar, pitch, dt_)
+    Bb = _dev_pitched(Bbar, pitch, dt_)
     jb = torch.zeros_like(Eb)
     wb = fmx.fmx_adjoint_workspace_bytes(ctypes.byref(g.params))
     work = torch.zeros(wb + 256, dtype=torch.uint8, device="cuda")
     wp = (work.data_ptr() + 255) // 256 * 256
     vp = lambda t: (ctypes.c_void_p * 3)(*[t[c].data_ptr() for c in range(3)])
-    fmx.check(fmx.fmx_adjoint_step(g.handle, vp(Eb), vp(Bb), vp(jb), wp, wb))
+    fmx.check(fmx.fmx_adjoint_step(g.handle, vp(Eb), vp(Bb), vp(jb) if with_jbar else None, wp, wb))
     torch.cuda.synchronize()
-    f = lambda t: t[..., :nx].cpu().numpy()
+    f = lambda t: t[..., :nx].double().cpu().numpy()
     return f(Eb), f(Bb), f(jb)
 
 
@@ -59,6 +60,42 @@ def test_adjoint_step_matches_oracle(fmx, shape, kw):
     Eg, Bg, jg = _adjoint_gpu(fmx, shape, Ebar, Bbar, courant=0.7, engine=1, **kw)
     Eo, Bo, jo = core.adjoint_step(core.Params(shape=shape, courant=0.7, **kw), Ebar, Bbar)
     assert rel_l2(Eg, Eo) < 1e-12 and rel_l2(Bg, Bo) < 1e-12 and rel_l2(jg, jo) < 1e-12
+
+
+@pytest.mark.parametrize("m", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("passes", [0, 1, 2, 3])
+def test_fused_adjoint_fp32_matches_oracle(fmx, m, passes):
+    """FP32 fused TE/TM adjoint kernels (grids on the fused engine), every
+    (m, passes) pair, several strips and segments, the periodic seam on both
+    sides, with and without jbar, against the oracle's adjoint with the
+    FP32-rounded coefficients."""
+    for shape in ((262, 97), (556, 61)):
+        Ebar, Bbar, _ = synth.random_fields(shape, seed=60 + m)
+        Ebar, Bbar = Ebar.astype(np.float32), Bbar.astype(np.float32)
+        kw = dict(m=m, filter_passes=passes, courant=0.8)
+        Eo, Bo, jo = core.adjoint_step(core.Params(shape=shape, coef_f32=True, **kw), Ebar.astype(np.float64),
+                                       Bbar.astype(np.float64))
+        Eg, Bg, jg = _adjoint_gpu(fmx, shape, Ebar, Bbar, precision=0, engine=2, **kw)
+        assert rel_l2(Eg, Eo) < 1e-5 and rel_l2(Bg, Bo) < 1e-5 and rel_l2(jg, jo) < 1e-5, (shape, m, passes)
+        Eg, Bg, _ = _adjoint_gpu(fmx, shape, Ebar, Bbar, precision=0, engine=2, with_jbar=False, **kw)
+        assert rel_l2(Eg, Eo) < 1e-5 and rel_l2(Bg, Bo) < 1e-5
+
+
+def test_dot_product_identity_fp32_fused(fmx):
+    """<T d, y> = <d, T^T y> in FP32 with the fused forward (TE/TM) and fused
+    adjoint kernels; bound from FP32 rounding of the two sums."""
+    shape = (300, 140)
+    dE, dB, dJ = (x.astype(np.float32) for x in synth.random_fields(shape, seed=44))
+    yE, yB, _ = (x.astype(np.float32) for x in synth.random_fields(shape, seed=45))
+    g = fmx.Grid(shape, precision=0, m=4, filter_passes=3, engine=2)
+    g.set_fields(dE, dB)
+    g.set_current(dJ)
+    g.step(1)
+    E1, B1, _ = g.get_fields()
+    lhs = np.sum(E1.astype(np.float64) * yE) + np.sum(B1.astype(np.float64) * yB)
+    Eb, Bb, jb = _adjoint_gpu(fmx, shape, yE, yB, precision=0, m=4, filter_passes=3, engine=2)
+    rhs = np.sum(dE * Eb) + np.sum(dB * Bb) + np.sum(dJ * jb)
+    assert abs(lhs - rhs) <= 1e-5 * (np.sum(np.abs(E1 * yE)) + np.sum(np.abs(B1 * yB)))
 
 
 def test_dot_product_identity_gpu(fmx):

@@ -133,6 +133,12 @@ def test_staged_fields_filter_and_lumped(fmx):
         Eg, Bg, _ = _run_gpu(fmx, shape, E, B, J, 4, precision=1, engine=eng, lumped=True, filter_passes=1)
         Eo, Bo, rc, _ = _oracle(shape, E, B, J, 4, lumped=True, filter_passes=1)
         assert_parity(Eg, Bg, Eo, Bo, TOL64, f"lumped engine {eng}")
+    # FP32 lumped with an even n_x: the fused engine's single-kernel path
+    E32, B32, J32 = (x.astype(np.float32) for x in (E, B, J))
+    Eg, Bg, _ = _run_gpu(fmx, shape, E32, B32, J32, 4, precision=0, engine=2, lumped=True, filter_passes=1)
+    Eo, Bo, rc, _ = _oracle(shape, E32.astype(np.float64), B32.astype(np.float64), J32.astype(np.float64), 4,
+                            lumped=True, filter_passes=1, coef_f32=True)
+    assert_parity(Eg, Bg, Eo, Bo, TOL32, "lumped fp32 fused")
 
 
 # ---------------------------------------------------------------------------
