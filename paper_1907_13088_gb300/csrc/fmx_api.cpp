@@ -294,17 +294,31 @@ template <typename T>
 fmx_status staged_step(fmx_grid *g) {
     const fmx::Coef<T> c = make_coef<T>(g->co);
     fmx::StagedPtrs<T> P = staged_ptrs<T>(g);
-    const T *jsrc[3];
-    fmx_status s = filtered_current<T>(g, jsrc);
-    if (s != FMX_OK) return s;
     const bool resid = g->p.iter_mode == FMX_ITER_RESIDUAL;
-    g->launches += fmx::launch_staged_source<T>(g->geo, g->p.dims, c, P, jsrc, g->stream, resid);
+    const bool have_j = g->buf.J[0] != nullptr;
+    const int jpasses = (have_j && g->p.filter_target == FMX_FILTER_CURRENT) ? g->p.filter_passes : 0;
+    // 3D, fixed m, at most one filter pass on the current: the z-marching
+    // kernels (source with the filter fused, sweeps from a plane ring)
+    const bool march = !resid && fmx::march3d_supported(g->p.dims, jpasses);
+    const T *jsrc[3];
+    fmx_status s = FMX_OK;
+    if (march) {
+        const T *jraw[3] = {have_j ? P.J[0] : nullptr, have_j ? P.J[1] : nullptr, have_j ? P.J[2] : nullptr};
+        const T *b[3] = {P.B[0], P.B[1], P.B[2]};
+        g->launches += fmx::launch_march3d_source<T>(g->geo, c, b, jraw, jpasses, P.dEp, g->stream);
+    } else {
+        s = filtered_current<T>(g, jsrc);
+        if (s != FMX_OK) return s;
+        g->launches += fmx::launch_staged_source<T>(g->geo, g->p.dims, c, P, jsrc, g->stream, resid);
+    }
     if (!resid) {
         const T *in[3] = {P.dEp[0], P.dEp[1], P.dEp[2]};
+        const T *dp[3] = {P.dEp[0], P.dEp[1], P.dEp[2]};
         for (int it = 0; it < g->p.m; ++it) {
             T *out[3];
             for (int q = 0; q < 3; ++q) out[q] = (it % 2 == 0) ? P.dEa[q] : P.dEb[q];
-            g->launches += fmx::launch_staged_sweep<T>(g->geo, g->p.dims, c, P, in, out, false, g->stream);
+            g->launches += march ? fmx::launch_march3d_sweep<T>(g->geo, c, dp, in, out, g->stream)
+                                 : fmx::launch_staged_sweep<T>(g->geo, g->p.dims, c, P, in, out, false, g->stream);
             for (int q = 0; q < 3; ++q) in[q] = out[q];
         }
         g->launches += fmx::launch_update_e<T>(g->geo, P.E, in, g->stream);

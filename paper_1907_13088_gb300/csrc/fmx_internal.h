@@ -82,6 +82,16 @@ int launch_update_e_resid(const Geo &g, const StagedPtrs<T> &p, cudaStream_t s);
 template <typename T>
 int launch_faraday(const Geo &g, int dims, const Coef<T> &c, T *const E[3], T *const B[3], cudaStream_t s);
 
+// 3D z-marching kernels (march3d.cu): source with at most one binomial pass
+// on the current fused in, and one sweep of Algorithm 1.
+bool march3d_supported(int dims, int passes);
+template <typename T>
+int launch_march3d_source(const Geo &g, const Coef<T> &c, const T *const B[3], const T *const J[3], int passes,
+                          T *const out[3], cudaStream_t s);
+template <typename T>
+int launch_march3d_sweep(const Geo &g, const Coef<T> &c, const T *const dEp[3], const T *const in[3], T *const out[3],
+                         cudaStream_t s);
+
 // Diagnostics (diag.cu): writes 6 FP64 values to out_dev (w_scheme sum,
 // w_plain sum, divb max, divb sum sq, gauss max, gauss sum sq).
 template <typename T>

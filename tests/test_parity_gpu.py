@@ -122,6 +122,26 @@ def test_staged_fp64_3d_1d(fmx, shape):
     assert_parity(Eg, Bg, Eo, Bo, TOL64, f"staged {shape}")
 
 
+@pytest.mark.parametrize("kw", [dict(m=4, filter_passes=0), dict(m=2, filter_passes=2), dict(m=1, filter_passes=1),
+                                dict(m=0, filter_passes=1)])
+def test_3d_march_and_staged_branches(fmx, kw):
+    """3D: the z-marching kernels (at most one filter pass on the current;
+    several z segments and tiles, ragged in every axis) and the staged
+    fallback (two passes), FP64 and FP32, with and without a current."""
+    shape = (37, 11, 70)
+    E, B, J = _inputs(shape, 33, np.float64)
+    for with_j in (True, False):
+        Jw = J if with_j else None
+        Eg, Bg, _ = _run_gpu(fmx, shape, E, B, Jw, 3, precision=1, engine=1, courant=0.6, **kw)
+        Eo, Bo, rc, _ = _oracle(shape, E, B, Jw, 3, courant=0.6, **kw)
+        assert_parity(Eg, Bg, Eo, Bo, TOL64, f"3d fp64 {kw} j={with_j}")
+    E32, B32, J32 = (x.astype(np.float32) for x in (E, B, J))
+    Eg, Bg, _ = _run_gpu(fmx, shape, E32, B32, J32, 3, precision=0, engine=1, courant=0.6, **kw)
+    Eo, Bo, rc, _ = _oracle(shape, E32.astype(np.float64), B32.astype(np.float64), J32.astype(np.float64), 3,
+                            courant=0.6, coef_f32=True, **kw)
+    assert_parity(Eg, Bg, Eo, Bo, TOL32, f"3d fp32 {kw}")
+
+
 def test_staged_fields_filter_and_lumped(fmx):
     shape = (24, 18)
     E, B, J = _inputs(shape, 41, np.float64)
