@@ -182,6 +182,10 @@ struct fmx_grid {
     double *diag_out = nullptr;
     fmx::DevStatus *st = nullptr;
     double *small = nullptr;  // kSmallDoubles doubles of workspace
+    // second stream for the TM chain of the fused 2D engine, with its fork
+    // and join events (created on first use)
+    cudaStream_t s_tm = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // Gaussian-source run (fmx_gauss_setup)
     int gauss_np = 0;
     double gauss_width = 0.0, gauss_omega0 = 0.0;
@@ -376,6 +380,21 @@ cudaEvent_t *profile_events(fmx_grid *g, size_t n) {
 template <typename T>
 fmx_status fused_step(fmx_grid *g, int nsteps) {
     const fmx::Coef<T> c = make_coef<T>(g->co);
+    // TE/TM kernels: the TE and TM chains touch disjoint components, so the TM
+    // launches go to a second stream, forked from and joined back into the
+    // grid's stream (not when profiling: the events time one stream)
+    bool two = false;
+    if constexpr (sizeof(T) == 4)
+        two = nsteps > 0 && !g->prof && fmx::fused2d_pol_supported(g->geo) && c.c6 == 1.f / 6.f;
+    if (two) {
+        cudaError_t e = cudaSuccess;
+        if (!g->s_tm) e = cudaStreamCreateWithFlags(&g->s_tm, cudaStreamNonBlocking);
+        if (e == cudaSuccess && !g->ev_fork) e = cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess && !g->ev_join) e = cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(g->ev_fork, g->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(g->s_tm, g->ev_fork, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "TM stream fork");
+    }
     for (int n = 0; n < nsteps; ++n) {
         const int nxt = 1 - g->cur;
         fmx::Fused2dArgs<T> a{};
@@ -393,7 +412,7 @@ fmx_status fused_step(fmx_grid *g, int nsteps) {
         if constexpr (sizeof(T) == 4) {
             // the TE/TM kernels take alpha's 1/6 as a compile-time constant (lumped mode zeroes it)
             if (fmx::fused2d_pol_supported(g->geo) && c.c6 == 1.f / 6.f) {
-                nl = fmx::launch_fused2d_pol(g->geo, c, a, g->stream, ev);
+                nl = fmx::launch_fused2d_pol(g->geo, c, a, g->stream, ev, two ? g->s_tm : nullptr);
                 g->prof_kinds = 2;
             } else {
                 if (ev) cudaEventRecord(ev[0], g->stream);
@@ -412,6 +431,11 @@ fmx_status fused_step(fmx_grid *g, int nsteps) {
         g->cur = nxt;
         g->last_sweeps = g->p.m;
         g->total_sweeps += g->p.m;
+    }
+    if (two) {
+        cudaError_t e = cudaEventRecord(g->ev_join, g->s_tm);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(g->stream, g->ev_join, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "TM stream join");
     }
     return check_launch(g, "fused step launch");
 }
@@ -1052,6 +1076,9 @@ fmx_status fmx_profile_read(fmx_grid *g, fmx_kernel_stat *out, int max, int *n) 
 void fmx_destroy(fmx_grid *g) {
     if (!g) return;
     for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
+    if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+    if (g->ev_join) cudaEventDestroy(g->ev_join);
+    if (g->s_tm) cudaStreamDestroy(g->s_tm);  // its work was joined into the grid's stream
     delete g;
 }
 

@@ -42,8 +42,9 @@ Fused2dShape fused2d_shape(const Geo &g, int m, int passes);
 // n_x (column pairs never straddle the periodic seam).  Returns the number
 // of kernels launched or -1.
 bool fused2d_pol_supported(const Geo &g);
+// s_tm: stream for the TM launch (nullptr: s); the caller orders the two
 int launch_fused2d_pol(const Geo &g, const Coef<float> &c, const Fused2dArgs<float> &a, cudaStream_t s,
-                       cudaEvent_t *ev = nullptr);
+                       cudaEvent_t *ev = nullptr, cudaStream_t s_tm = nullptr);
 Fused2dShape fused2d_pol_shape(const Geo &g, int m, int passes);
 
 // Fused 2D adjoint step (adjoint2d.cu), FP32, TE and TM kernels.  Maps

@@ -512,8 +512,10 @@ struct PolLauncher {
     }
 };
 
-// events (optional): ev[0] before the TE launch, ev[1] between, ev[2] after TM
+// events (optional): ev[0] before the TE launch, ev[1] between, ev[2] after TM;
+// the TM launch goes to t_tm when set
 thread_local cudaEvent_t *t_ev = nullptr;
+thread_local cudaStream_t t_tm = nullptr;
 
 template <int M, int P, bool HJ>
 int run_both(const Geo &g, const Coef2 &c, const Fused2dArgs<float> &a, cudaStream_t s, Fused2dShape *sh) {
@@ -524,7 +526,7 @@ int run_both(const Geo &g, const Coef2 &c, const Fused2dArgs<float> &a, cudaStre
     if (t_ev) cudaEventRecord(t_ev[0], s);
     PolLauncher<TE, M, P, HJ>::run(g, c, a, s);
     if (t_ev) cudaEventRecord(t_ev[1], s);
-    PolLauncher<TM, M, P, HJ>::run(g, c, a, s);
+    PolLauncher<TM, M, P, HJ>::run(g, c, a, t_tm ? t_tm : s);
     if (t_ev) cudaEventRecord(t_ev[2], s);
     return 2;
 }
@@ -574,13 +576,15 @@ Coef2 make_coef2(const Coef<float> &c, int passes) {
 bool fused2d_pol_supported(const Geo &g) { return g.nx % 2 == 0 && (int64_t)g.ny * g.pitch < ((int64_t)1 << 31); }
 
 int launch_fused2d_pol(const Geo &g, const Coef<float> &c, const Fused2dArgs<float> &a, cudaStream_t s,
-                       cudaEvent_t *ev) {
+                       cudaEvent_t *ev, cudaStream_t s_tm) {
     const bool hj = a.J[0] != nullptr;
     const int p = hj ? a.passes : 0;
     if (c.c6 != 1.f / 6.f) return -1;  // the kernels use 1/6 as a compile-time constant
     t_ev = ev;
+    t_tm = s_tm;
     const int n = pol_dispatch(g, make_coef2(c, p), a, s, a.m, hj, p, nullptr);
     t_ev = nullptr;
+    t_tm = nullptr;
     return n;
 }
 
