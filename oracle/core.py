@@ -50,7 +50,8 @@ class _Params(ctypes.Structure):
                 ("c", ctypes.c_double), ("dt", ctypes.c_double), ("m", ctypes.c_int),
                 ("residual", ctypes.c_int), ("tol", ctypes.c_double), ("m_max", ctypes.c_int),
                 ("filter_passes", ctypes.c_int), ("filter_target", ctypes.c_int),
-                ("lumped", ctypes.c_int), ("coef_f32", ctypes.c_int)]
+                ("lumped", ctypes.c_int), ("coef_f32", ctypes.c_int), ("cheb", ctypes.c_int),
+                ("cheb_lo", ctypes.c_double), ("cheb_hi", ctypes.c_double)]
 
 
 class _Stats(ctypes.Structure):
@@ -141,6 +142,7 @@ class Params:
     filter_target: int = FILTER_CURRENT
     lumped: bool = False
     coef_f32: bool = False
+    cheb: bool = False  # Chebyshev acceleration of the solve (spectral.a_interval)
 
     @property
     def dims(self) -> int:
@@ -181,6 +183,10 @@ class Params:
         p.filter_target = self.filter_target
         p.lumped = int(self.lumped)
         p.coef_f32 = int(self.coef_f32)
+        p.cheb = int(self.cheb)
+        if self.cheb:
+            from . import spectral
+            p.cheb_lo, p.cheb_hi = spectral.a_interval(self)
         return p
 
 

@@ -324,8 +324,66 @@ static double sumsq(long n, const double *a)
  * whose update satisfies ||dE_(s+1) - dE_(s)||_2 <= tol ||dEp||_2 (L2 over
  * all three components); dEp = 0 needs no sweep; no convergence within m_max
  * sweeps returns ORC_ENOCONV.  *sweeps and *resid report what happened. */
+/* Chebyshev acceleration of the solve (1 - A) x = dE' (the textbook
+ * three-term recurrence of Chebyshev semi-iteration for a symmetric matrix
+ * whose spectrum lies in [al, be]; here M = 1 - A, al = 1 - cheb_hi,
+ * be = 1 - cheb_lo).  x_0 = dE' as in Algorithm 1; every sweep applies A once:
+ *   r_k = dE' - x_k + A x_k,  d_k = rho_k rho_{k-1} d_{k-1} + (2 rho_k / delta) r_k,
+ *   x_{k+1} = x_k + d_k,  rho_0 = delta / theta, rho_k = 1 / (2 theta / delta - rho_{k-1}),
+ * with theta = (be + al)/2, delta = (be - al)/2 and d_0 = r_0 / theta.  The
+ * stop rule of residual mode is the same as for Algorithm 1: ||d_k|| <= tol
+ * ||dE'||. */
+static int solve_chebyshev(const orc_params *p, const double *dEp, double *x, int *sweeps, double *resid)
+{
+    shape_t s = shape_of(p);
+    const long n3 = 3 * s.ncell;
+    double *Ax = (double *)calloc((size_t)n3, sizeof(double));
+    double *d = (double *)calloc((size_t)n3, sizeof(double));
+    memcpy(x, dEp, sizeof(double) * n3);
+    const double al = 1.0 - p->cheb_hi, be = 1.0 - p->cheb_lo;
+    const double theta = 0.5 * (be + al), delta = 0.5 * (be - al);
+    const double sig = theta / delta;
+    double rho = 1.0 / sig;
+    const double nrm = sqrt(sumsq(n3, dEp));
+    const int cap = p->residual ? p->m_max : p->m;
+    int rc = (p->residual && nrm > 0.0) ? ORC_ENOCONV : ORC_OK;
+    int done = 0;
+    double r = 0.0;
+    for (int k = 0; k < cap && !(p->residual && nrm == 0.0); ++k) {
+        orc_apply_A(p, x, Ax);
+        double c1, c2;
+        if (k == 0) {
+            c1 = 0.0;
+            c2 = 1.0 / theta;
+        } else {
+            const double rho_new = 1.0 / (2.0 * sig - rho);
+            c1 = rho_new * rho;
+            c2 = 2.0 * rho_new / delta;
+            rho = rho_new;
+        }
+        double dd = 0.0;
+        for (long c = 0; c < n3; ++c) {
+            const double rk = dEp[c] - x[c] + Ax[c];
+            d[c] = c1 * d[c] + c2 * rk;
+            x[c] += d[c];
+            dd += d[c] * d[c];
+        }
+        ++done;
+        if (p->residual) {
+            r = sqrt(dd) / nrm;
+            if (r <= p->tol) { rc = ORC_OK; break; }
+        }
+    }
+    free(Ax);
+    free(d);
+    if (sweeps) *sweeps = done;
+    if (resid) *resid = r;
+    return rc;
+}
+
 int orc_solve(const orc_params *p, const double *dEp, double *dE, int *sweeps, double *resid)
 {
+    if (p->cheb) return solve_chebyshev(p, dEp, dE, sweeps, resid);
     shape_t s = shape_of(p);
     const long n3 = 3 * s.ncell;
     double *Ad = (double *)calloc((size_t)n3, sizeof(double));

@@ -39,6 +39,9 @@ typedef struct {
     int filter_target; /* ORC_FILTER_* */
     int lumped;        /* 1: alpha -> 1 (Yee) */
     int coef_f32;      /* 1: round every coefficient to binary32 */
+    int cheb;          /* 1: Chebyshev acceleration of the solve (m sweeps, or to tol) */
+    double cheb_lo;    /* interval [cheb_lo, cheb_hi] holding the eigenvalues of A */
+    double cheb_hi;
 } orc_params;
 
 typedef struct {

@@ -162,6 +162,47 @@ def exact_inverse(p, dEp):
     return _from_phys(p, _solve3(A, F), E_OFF)
 
 
+def a_interval(p, samples=33, widen=0.01):
+    """Interval [lo, hi] holding the eigenvalues of A for the Chebyshev mode:
+    the extreme eigenvalues of the real symmetric 3x3 symbol over s_i^2 =
+    j / (samples - 1), j = 0 .. samples - 1, on every active axis (s_i =
+    sin(k_i d_i / 2); the signs of the s_i do not change the eigenvalues),
+    widened by widen * (1 - hi) at both ends."""
+    g = np.linspace(0.0, 1.0, samples)
+    axes = [g if a < p.dims else np.zeros(1) for a in range(3)]
+    S = np.stack(np.meshgrid(*axes, indexing="ij"), -1).reshape(-1, 3)
+    kd = tuple(2.0 * np.arcsin(np.sqrt(S[:, a])) for a in range(3))
+    _, _, A = symbols(p, kd)
+    n = S.shape[0]
+    M = np.empty((n, 3, 3))
+    for i in range(3):
+        for j in range(3):
+            M[:, i, j] = np.broadcast_to(np.real(np.asarray(A[i][j])), (n,))
+    w = np.linalg.eigvalsh(M)
+    lo, hi = float(w.min()), float(w.max())
+    return lo - widen * (1.0 - hi), hi + widen * (1.0 - hi)
+
+
+def chebyshev_error_poly(t, m, lo, hi):
+    """Chebyshev semi-iteration's error polynomial P_m(t) = T_m((theta - t) /
+    delta) / T_m(theta / delta) for M = 1 - A with spectrum in [1 - hi, 1 - lo]
+    (theta, delta: centre and half-width); T_m evaluated as cos(m acos x) or
+    cosh(m acosh |x|) sign(x)^m."""
+    al, be = 1.0 - hi, 1.0 - lo
+    theta, delta = 0.5 * (be + al), 0.5 * (be - al)
+
+    def T(x):
+        x = np.asarray(x, dtype=float)
+        inside = np.abs(x) <= 1.0
+        out = np.empty_like(x)
+        out[inside] = np.cos(m * np.arccos(x[inside]))
+        xo = x[~inside]
+        out[~inside] = np.cosh(m * np.arccosh(np.abs(xo))) * np.sign(xo) ** m
+        return out
+
+    return T((theta - np.asarray(t, dtype=float)) / delta) / T(np.array([theta / delta]))[0]
+
+
 def A_matrix(p, kd):
     """Real symmetric 3x3 symbol of A at one wavevector kd = (kx dx, ky dy, kz dz)."""
     _, _, A = symbols(p, tuple(np.array([v]) for v in kd))

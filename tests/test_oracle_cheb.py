@@ -1,0 +1,81 @@
+"""Oracle pins of the Chebyshev-accelerated solve (the next-row iteration mode:
+Chebyshev semi-iteration for (1 - A) dE = dE' on the spectral interval of A).
+
+The result of m sweeps is pinned, wavevector by wavevector, against the
+closed-form Chebyshev error polynomial applied to the exact inverse's error:
+x_m = x* + P_m(M)(dE' - x*), M = 1 - A, x* = M^{-1} dE', evaluated with the
+per-k symbol of A (a second derivation, spectral.py) and an eigendecomposition.
+Residual mode must land on the exact inverse, in fewer sweeps than Algorithm 1.
+"""
+import numpy as np
+import pytest
+
+from oracle import core, spectral
+from paper_1907_13088_gb300 import synth
+from tests.helpers import rel_l2
+
+E_OFF = spectral.E_OFF
+
+
+def _per_k_expected(p, b, m):
+    """x* + P_m(M)(b - x*) per wavevector, back in real space."""
+    _, _, A = spectral.symbols(p)
+    B = spectral._to_phys(p, b, E_OFF)
+    shp = B.shape[1:]
+    Mk = np.zeros(shp + (3, 3))
+    for i in range(3):
+        for j in range(3):
+            Mk[..., i, j] = (1.0 if i == j else 0.0) - np.broadcast_to(np.real(A[i][j]), shp)
+    lo, hi = spectral.a_interval(p)
+    w, V = np.linalg.eigh(Mk)
+    # x* = V diag(1/w) V^T b;  x_m = x* + V diag(P_m(w)) V^T (b - x*) = V diag(1/w + P_m(w)(1 - 1/w)) V^T b
+    Pm = spectral.chebyshev_error_poly(w.ravel(), m, lo, hi).reshape(w.shape)
+    g = 1.0 / w + Pm * (1.0 - 1.0 / w)
+    bk = np.moveaxis(B, 0, -1)[..., None]
+    xk = V @ (g[..., None] * (np.swapaxes(V, -1, -2) @ bk))
+    return spectral._from_phys(p, np.moveaxis(xk[..., 0], -1, 0), E_OFF)
+
+
+@pytest.mark.parametrize("shape,courant", [((16, 12), 0.5), ((16, 12), 0.95), ((8, 6, 5), 0.6), ((24,), 0.9)])
+@pytest.mark.parametrize("m", [1, 2, 5, 9])
+def test_chebyshev_matches_error_polynomial_per_k(shape, courant, m):
+    p = core.Params(shape=shape, courant=courant, m=m, cheb=True)
+    b = synth.random_fields(shape, seed=70 + m)[0]
+    x, rc, sweeps, _ = core.solve(p, b)
+    assert rc == 0
+    assert sweeps == m
+    ref = _per_k_expected(p, b, m)
+    assert rel_l2(x, ref) < 1e-12, rel_l2(x, ref)
+
+
+@pytest.mark.parametrize("shape,courant", [((32, 32), 0.5), ((10, 8, 6), 0.5), ((32, 32), 0.99)])
+def test_chebyshev_residual_reaches_exact_inverse_faster(shape, courant):
+    b = synth.random_fields(shape, seed=80)[0]
+    pc = core.Params(shape=shape, courant=courant, residual=True, tol=1e-13, cheb=True)
+    pj = core.Params(shape=shape, courant=courant, residual=True, tol=1e-13)
+    xc, rc, nc, _ = core.solve(pc, b)
+    assert rc == 0
+    xj, rcj, nj, _ = core.solve(pj, b)
+    exact = spectral.exact_inverse(pc, b)
+    assert rel_l2(xc, exact) < 1e-11 and rel_l2(xj, exact) < 1e-11
+    # rate: ((sqrt(kappa) - 1) / (sqrt(kappa) + 1)) per sweep against lambda_max for Algorithm 1
+    lo, hi = spectral.a_interval(pc)
+    kappa = (1.0 - lo) / (1.0 - hi)
+    q = (np.sqrt(kappa) - 1.0) / (np.sqrt(kappa) + 1.0)
+    assert nc <= int(np.ceil(np.log(2.0 / 1e-13) / np.log(1.0 / q))) + 2
+    assert nc < 0.6 * nj, (nc, nj)
+
+
+def test_interval_holds_the_grid_spectrum():
+    """The sampled, widened interval contains every eigenvalue of A on a grid."""
+    for shape, cf in (((32, 32), 0.5), ((12, 10, 8), 0.7), ((64,), 0.3)):
+        p = core.Params(shape=shape, courant=cf)
+        lo, hi = spectral.a_interval(p)
+        _, _, A = spectral.symbols(p)
+        shp = np.broadcast(*[np.asarray(A[i][j]) for i in range(3) for j in range(3)]).shape
+        M = np.zeros(shp + (3, 3))
+        for i in range(3):
+            for j in range(3):
+                M[..., i, j] = np.broadcast_to(np.real(A[i][j]), shp)
+        w = np.linalg.eigvalsh(M)
+        assert w.min() >= lo and w.max() <= hi and hi < 1.0
