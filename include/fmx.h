@@ -64,7 +64,14 @@ typedef enum {
 } fmx_status;
 
 enum { FMX_F32 = 0, FMX_F64 = 1 };                        /* storage and sweep precision */
-enum { FMX_ITER_FIXED = 0, FMX_ITER_RESIDUAL = 1 };       /* Algorithm 1 stop rule       */
+/* Solve of (1 - A) dE = dE' (Eq. transform-e-e_aux): Algorithm 1 with m sweeps or
+ * to a residual, or Chebyshev semi-iteration (the paper's suggested faster
+ * iteration, not its method: the textbook three-term recurrence on an
+ * interval holding the eigenvalues of A, see fmx_cheb_interval), m sweeps
+ * or to a residual.  Every mode applies A once per sweep; the residual is
+ * ||x_(s+1) - x_(s)|| / ||dE'|| in all of them.  The Chebyshev modes run on
+ * the staged engine. */
+enum { FMX_ITER_FIXED = 0, FMX_ITER_RESIDUAL = 1, FMX_ITER_CHEB_FIXED = 2, FMX_ITER_CHEB_RESIDUAL = 3 };
 enum { FMX_FILTER_NONE = 0, FMX_FILTER_CURRENT = 1, FMX_FILTER_FIELDS = 2 };
 enum { FMX_ENGINE_AUTO = 0, FMX_ENGINE_STAGED = 1, FMX_ENGINE_FUSED = 2 };
 enum { FMX_HOST = 0, FMX_DEVICE = 1 };                    /* where a copy source/target lives */
@@ -94,10 +101,10 @@ typedef struct {
     double dt;           /* time step; if <= 0, dt = courant * dt_CFL                   */
     double courant;      /* fraction of dt_CFL used when dt <= 0, in (0, 1]             */
     int precision;       /* FMX_F32 or FMX_F64                                          */
-    int iter_mode;       /* FMX_ITER_FIXED or FMX_ITER_RESIDUAL                         */
-    int m;               /* sweeps of Algorithm 1 in fixed mode, >= 0                   */
-    double tol;          /* residual mode: stop when ||dE_(s+1)-dE_(s)|| <= tol ||dE'|| */
-    int m_max;           /* residual mode: sweep cap (FMX_ENOCONV beyond)               */
+    int iter_mode;       /* FMX_ITER_*                                                   */
+    int m;               /* sweeps in the fixed modes, >= 0                             */
+    double tol;          /* residual modes: stop when ||dE_(s+1)-dE_(s)|| <= tol ||dE'|| */
+    int m_max;           /* residual modes: sweep cap (FMX_ENOCONV beyond)              */
     int filter_passes;   /* binomial (1/4,1/2,1/4) passes per active axis, >= 0         */
     int filter_target;   /* FMX_FILTER_NONE / _CURRENT (each step, before the source) / _FIELDS (after the update) */
     int lumped;          /* 1: alpha -> 1, A = 0 (the Yee scheme, Sec. 2)               */
@@ -209,6 +216,13 @@ fmx_status fmx_coefficients(const fmx_grid *g, double *out, int n);
 
 /* dt in use (after courant * dt_CFL). */
 double fmx_time_step(const fmx_grid *g);
+
+/* Chebyshev modes: the interval [lo, hi] taken to hold the eigenvalues of A --
+ * the extreme eigenvalues of the real symmetric 3x3 symbol of A (Eqs.
+ * matrixA_1st..last with Dbar_a -> 2 i s_a, s_a = sin(k_a d_a / 2)) over
+ * s_a^2 = j/32, j = 0..32, on every active axis, widened by 0.01 (1 - hi) at
+ * both ends.  Errors: FMX_EINVAL (NULL), FMX_ESTATE (not a Chebyshev mode). */
+fmx_status fmx_cheb_interval(const fmx_grid *g, double *lo, double *hi);
 
 /* Device pointer of component c (0..5: Ex..Bz of the current state set,
  * 6..8: Jx..Jz), or NULL. */

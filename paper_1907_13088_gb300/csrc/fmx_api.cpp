@@ -64,6 +64,78 @@ int resolve_engine(const fmx_params *p) {
     return fusable ? FMX_ENGINE_FUSED : FMX_ENGINE_STAGED;
 }
 
+// Eigenvalues of a real symmetric 3x3 matrix by cyclic Jacobi rotations:
+// each rotation in the (p, q) plane by the angle phi with tan(2 phi) =
+// 2 a_pq / (a_qq - a_pp) zeroes a_pq; the diagonal converges to the eigenvalues.
+void eig_sym3(double a[3][3], double w[3]) {
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        const double off = fabs(a[0][1]) + fabs(a[0][2]) + fabs(a[1][2]);
+        const double dia = fabs(a[0][0]) + fabs(a[1][1]) + fabs(a[2][2]);
+        if (off <= 1e-17 * dia || off == 0.0) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (a[p][q] == 0.0) continue;
+                const double th = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+                const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+                // a <- G^T a G, G the rotation (cs, sn) in the (p, q) plane
+                double b[3][3];
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) b[i][j] = a[i][j];
+                for (int k = 0; k < 3; ++k) {
+                    b[k][p] = cs * a[k][p] - sn * a[k][q];
+                    b[k][q] = sn * a[k][p] + cs * a[k][q];
+                }
+                for (int k = 0; k < 3; ++k) {
+                    a[p][k] = cs * b[p][k] - sn * b[q][k];
+                    a[q][k] = sn * b[p][k] + cs * b[q][k];
+                    if (k != p && k != q) a[k][p] = a[p][k], a[k][q] = a[q][k];
+                }
+                a[p][p] = cs * b[p][p] - sn * b[q][p];
+                a[q][q] = sn * b[p][q] + cs * b[q][q];
+                a[p][q] = a[q][p] = 0.0;
+            }
+    }
+    for (int i = 0; i < 3; ++i) w[i] = a[i][i];
+}
+
+// The Chebyshev interval of fmx_cheb_interval from the step's coefficients
+// (co: FMX_NCOEF values in the fmx_coefficients order).
+void cheb_interval(int dims, const double *co, double *lo_out, double *hi_out) {
+    const double ad[3] = {co[5], co[6], co[7]};
+    const double apair[3] = {co[8], co[9], co[10]};  // coefficient of Dbar_bb Dbar_cc in A_aa
+    const double bcross[3] = {co[11], co[12], co[13]};  // A_ab by the third axis
+    const double c6 = co[4];
+    double lo = 1e300, hi = -1e300;
+    const int ns = 33;
+    const int n1 = dims > 1 ? ns : 1, n2 = dims > 2 ? ns : 1;
+    for (int i0 = 0; i0 < ns; ++i0)
+        for (int i1 = 0; i1 < n1; ++i1)
+            for (int i2 = 0; i2 < n2; ++i2) {
+                const double s2[3] = {i0 / 32.0, dims > 1 ? i1 / 32.0 : 0.0, dims > 2 ? i2 / 32.0 : 0.0};
+                double sv[3], dd[3];
+                for (int a = 0; a < 3; ++a) {
+                    sv[a] = sqrt(s2[a]);
+                    dd[a] = -4.0 * s2[a];  // Dbar_aa -> -4 s_a^2
+                }
+                double A[3][3];
+                for (int a = 0; a < 3; ++a) {
+                    const int b = (a + 1) % 3, c = (a + 2) % 3;
+                    A[a][a] = ad[b] * dd[b] + ad[c] * dd[c] + apair[a] * dd[b] * dd[c];
+                    // A_ab = b_ab Dbar_a Dbar_b (1 + Dbar_cc / 6) -> -4 b_ab s_a s_b (1 + c6 dd_c)
+                    A[a][b] = A[b][a] = -4.0 * bcross[c] * sv[a] * sv[b] * (1.0 + c6 * dd[c]);
+                }
+                double w[3];
+                eig_sym3(A, w);
+                for (int k = 0; k < 3; ++k) {
+                    lo = w[k] < lo ? w[k] : lo;
+                    hi = w[k] > hi ? w[k] : hi;
+                }
+            }
+    *lo_out = lo - 0.01 * (1.0 - hi);
+    *hi_out = hi + 0.01 * (1.0 - hi);
+}
+
 fmx_status validate(const fmx_params *p, double *dt_out, int *warn) {
     if (!p) return fail(FMX_EINVAL, "params is NULL");
     if (p->dims < 1 || p->dims > 3) return fail(FMX_EINVAL, "dims must be 1, 2 or 3 (got %d)", p->dims);
@@ -74,9 +146,10 @@ fmx_status validate(const fmx_params *p, double *dt_out, int *warn) {
     }
     if (!(p->c > 0.0)) return fail(FMX_EINVAL, "c must be > 0");
     if (p->precision != FMX_F32 && p->precision != FMX_F64) return fail(FMX_EINVAL, "bad precision");
-    if (p->iter_mode != FMX_ITER_FIXED && p->iter_mode != FMX_ITER_RESIDUAL) return fail(FMX_EINVAL, "bad iter_mode");
-    if (p->iter_mode == FMX_ITER_FIXED && (p->m < 0 || p->m > 1 << 20)) return fail(FMX_EINVAL, "m out of range");
-    if (p->iter_mode == FMX_ITER_RESIDUAL && (!(p->tol > 0.0) || p->m_max < 1))
+    if (p->iter_mode < FMX_ITER_FIXED || p->iter_mode > FMX_ITER_CHEB_RESIDUAL) return fail(FMX_EINVAL, "bad iter_mode");
+    const bool fixed = p->iter_mode == FMX_ITER_FIXED || p->iter_mode == FMX_ITER_CHEB_FIXED;
+    if (fixed && (p->m < 0 || p->m > 1 << 20)) return fail(FMX_EINVAL, "m out of range");
+    if (!fixed && (!(p->tol > 0.0) || p->m_max < 1))
         return fail(FMX_EINVAL, "residual mode needs tol > 0 and m_max >= 1");
     if (p->filter_passes < 0 || p->filter_passes > 1024) return fail(FMX_EINVAL, "filter_passes out of range");
     if (p->filter_target < FMX_FILTER_NONE || p->filter_target > FMX_FILTER_FIELDS)
@@ -186,6 +259,10 @@ struct fmx_grid {
     // and join events (created on first use)
     cudaStream_t s_tm = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // Chebyshev modes: the interval holding the eigenvalues of A, and the
+    // recurrence's constants
+    double cheb_lo = 0.0, cheb_hi = 0.0;
+    fmx::ChebParams cheb{1.0, 1.0, 1.0};
     // Gaussian-source run (fmx_gauss_setup)
     int gauss_np = 0;
     double gauss_width = 0.0, gauss_omega0 = 0.0;
@@ -298,12 +375,14 @@ template <typename T>
 fmx_status staged_step(fmx_grid *g) {
     const fmx::Coef<T> c = make_coef<T>(g->co);
     fmx::StagedPtrs<T> P = staged_ptrs<T>(g);
-    const bool resid = g->p.iter_mode == FMX_ITER_RESIDUAL;
+    const int mode = g->p.iter_mode;
+    const bool cheb = mode == FMX_ITER_CHEB_FIXED || mode == FMX_ITER_CHEB_RESIDUAL;
+    const bool resid = mode == FMX_ITER_RESIDUAL || mode == FMX_ITER_CHEB_RESIDUAL;
     const bool have_j = g->buf.J[0] != nullptr;
     const int jpasses = (have_j && g->p.filter_target == FMX_FILTER_CURRENT) ? g->p.filter_passes : 0;
-    // 3D, fixed m, at most one filter pass on the current: the z-marching
-    // kernels (source with the filter fused, sweeps from a plane ring)
-    const bool march = !resid && fmx::march3d_supported(g->p.dims, jpasses);
+    // 3D, Algorithm 1 with fixed m, at most one filter pass on the current: the
+    // z-marching kernels (source with the filter fused, sweeps from a plane ring)
+    const bool march = mode == FMX_ITER_FIXED && fmx::march3d_supported(g->p.dims, jpasses);
     const T *jsrc[3];
     fmx_status s = FMX_OK;
     if (march) {
@@ -313,9 +392,10 @@ fmx_status staged_step(fmx_grid *g) {
     } else {
         s = filtered_current<T>(g, jsrc);
         if (s != FMX_OK) return s;
-        g->launches += fmx::launch_staged_source<T>(g->geo, g->p.dims, c, P, jsrc, g->stream, resid);
+        // the solve's device-side status starts from ||dE'|| (residual and Chebyshev modes)
+        g->launches += fmx::launch_staged_source<T>(g->geo, g->p.dims, c, P, jsrc, g->stream, resid || cheb);
     }
-    if (!resid) {
+    if (mode == FMX_ITER_FIXED) {
         const T *in[3] = {P.dEp[0], P.dEp[1], P.dEp[2]};
         const T *dp[3] = {P.dEp[0], P.dEp[1], P.dEp[2]};
         for (int it = 0; it < g->p.m; ++it) {
@@ -329,20 +409,33 @@ fmx_status staged_step(fmx_grid *g) {
         g->last_sweeps = g->p.m;
         g->total_sweeps += g->p.m;
     } else {
+        // sweeps counted on the device (DevStatus): Algorithm 1 to a residual, or
+        // Chebyshev acceleration for m sweeps or to a residual
         g->launches += fmx::launch_resid_init(g->partials, g->nparts, g->st, g->stream);
         fmx::DevStatus hs;
         const double tol2 = g->p.tol * g->p.tol;
-        for (;;) {
-            for (int q = 0; q < 8; ++q) {
+        auto sweep = [&]() {
+            if (cheb) {
+                g->launches += fmx::launch_cheb_sweep<T>(g->geo, g->p.dims, c, P, g->cheb, g->stream);
+                g->launches += fmx::launch_cheb_update(g->partials, g->nparts, g->st, g->cheb, resid, tol2,
+                                                       g->p.m_max, g->stream);
+            } else {
                 g->launches += fmx::launch_resid_sweep<T>(g->geo, g->p.dims, c, P, g->stream);
                 g->launches += fmx::launch_resid_update(g->partials, g->nparts, g->st, tol2, g->p.m_max, g->stream);
             }
+        };
+        if (!resid) {  // Chebyshev, fixed m
+            for (int it = 0; it < g->p.m; ++it) sweep();
+        }
+        for (;;) {
+            if (resid)
+                for (int q = 0; q < 8; ++q) sweep();
             s = check_launch(g, "residual sweep launch");
             if (s != FMX_OK) return s;
             cudaError_t e = cudaMemcpyAsync(&hs, g->st, sizeof(hs), cudaMemcpyDeviceToHost, g->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
             if (e != cudaSuccess) return cuda_fail(e, "residual status read-back");
-            if (hs.done) break;
+            if (hs.done || !resid) break;
         }
         g->launches += fmx::launch_update_e_resid<T>(g->geo, P, g->stream);
         g->last_sweeps = hs.count;
@@ -589,6 +682,13 @@ fmx_status fmx_create(const fmx_params *p, fmx_grid **out, int *warnings) {
     g->p = *p;
     g->dt = dt;
     coefficients(p, dt, g->co);
+    if (p->iter_mode == FMX_ITER_CHEB_FIXED || p->iter_mode == FMX_ITER_CHEB_RESIDUAL) {
+        cheb_interval(p->dims, g->co, &g->cheb_lo, &g->cheb_hi);
+        const double al = 1.0 - g->cheb_hi, be = 1.0 - g->cheb_lo;
+        g->cheb.theta = 0.5 * (be + al);
+        g->cheb.delta = 0.5 * (be - al);
+        g->cheb.sig = g->cheb.theta / g->cheb.delta;
+    }
     g->engine = resolve_engine(p);
     g->geo = geo_of(p);
     g->elem = elem_size(p->precision);
@@ -1007,6 +1107,15 @@ fmx_status fmx_coefficients(const fmx_grid *g, double *out, int n) {
 }
 
 double fmx_time_step(const fmx_grid *g) { return g ? g->dt : 0.0; }
+
+fmx_status fmx_cheb_interval(const fmx_grid *g, double *lo, double *hi) {
+    if (!g || !lo || !hi) return fail(FMX_EINVAL, "NULL argument");
+    if (g->p.iter_mode != FMX_ITER_CHEB_FIXED && g->p.iter_mode != FMX_ITER_CHEB_RESIDUAL)
+        return fail(FMX_ESTATE, "not a Chebyshev mode");
+    *lo = g->cheb_lo;
+    *hi = g->cheb_hi;
+    return FMX_OK;
+}
 
 void *fmx_field_ptr(const fmx_grid *g, int c) {
     if (!g || !g->bound || c < 0 || c > 8) return nullptr;

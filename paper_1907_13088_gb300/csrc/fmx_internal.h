@@ -35,6 +35,13 @@ struct DevStatus {
     int done;        // 1 when the current solve stopped
     int noconv;      // 1 when it stopped at m_max
     int err;         // latched device error (FMX_ETIMEOUT, ...)
+    double cheb_rho; // Chebyshev mode: rho of the last sweep
+};
+
+// Chebyshev acceleration: M = 1 - A has its spectrum in [1 - hi, 1 - lo];
+// theta, delta = centre and half-width, sig = theta / delta
+struct ChebParams {
+    double theta, delta, sig;
 };
 
 // Pointers of one staged step (all device).
@@ -71,6 +78,15 @@ template <typename T>
 int launch_resid_sweep(const Geo &g, int dims, const Coef<T> &c, const StagedPtrs<T> &p, cudaStream_t s);
 
 int launch_resid_init(double *partials, int64_t nparts, DevStatus *st, cudaStream_t s);
+
+// Chebyshev sweep s = st->count (x in dEp / dEa / dEb by the parity of s as in
+// residual mode, the search direction d in jf, updated in place), then the
+// single-block update (||d||^2, rho, count; stop test when resid)
+template <typename T>
+int launch_cheb_sweep(const Geo &g, int dims, const Coef<T> &c, const StagedPtrs<T> &p, const ChebParams &cp,
+                      cudaStream_t s);
+int launch_cheb_update(double *partials, int64_t nparts, DevStatus *st, const ChebParams &cp, bool resid,
+                       double tol2, int m_max, cudaStream_t s);
 int launch_resid_update(double *partials, int64_t nparts, DevStatus *st, double tol2, int m_max, cudaStream_t s);
 
 template <typename T>

@@ -130,6 +130,47 @@ __global__ void k_resid_sweep(Geo g, Coef<T> c, StagedPtrs<T> P) {
     block_sum_to(v, P.partials);
 }
 
+// Chebyshev semi-iteration (textbook three-term recurrence) for
+// (1 - A) x = dE', x_0 = dE': sweep s computes r = dE' - x_s + A x_s,
+// d = c1 d + c2 r, x_{s+1} = x_s + d, with c1 = 0, c2 = 1/theta for s = 0 and
+// rho_s = 1 / (2 sig - rho_{s-1}), c1 = rho_s rho_{s-1}, c2 = 2 rho_s / delta
+// after (rho_0 = 1 / sig, kept in DevStatus.cheb_rho by the update kernel).
+template <typename T, int DIM>
+__global__ void k_cheb_sweep(Geo g, Coef<T> c, StagedPtrs<T> P, ChebParams cp) {
+    if (P.st->done) return;
+    const int s = P.st->count;
+    double c1 = 0.0, c2 = 1.0 / cp.theta;
+    if (s > 0) {
+        const double rp = P.st->cheb_rho, rn = 1.0 / (2.0 * cp.sig - rp);
+        c1 = rn * rp;
+        c2 = 2.0 * rn / cp.delta;
+    }
+    Pos p;
+    int64_t idx;
+    bool inb = cell(g, p, idx);
+    double v = 0.0;
+    if (inb) {
+        const T *in[3];
+        T *out[3];
+        for (int q = 0; q < 3; ++q) {
+            in[q] = s == 0 ? P.dEp[q] : ((s & 1) ? P.dEa[q] : P.dEb[q]);
+            out[q] = ((s + 1) & 1) ? P.dEa[q] : P.dEb[q];
+        }
+        Field<T, T> f[3] = {{in[0], g}, {in[1], g}, {in[2], g}};
+        const T ax[3] = {apply_a<T, DIM, 0>(f, p, c), apply_a<T, DIM, 1>(f, p, c), apply_a<T, DIM, 2>(f, p, c)};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const T x = in[q][idx];
+            const T r = P.dEp[q][idx] - x + ax[q];
+            const T d = (s == 0 ? T(0) : T(c1) * P.jf[q][idx]) + T(c2) * r;
+            P.jf[q][idx] = d;
+            out[q][idx] = x + d;
+            v += (double)d * (double)d;
+        }
+    }
+    block_sum_to(v, P.partials);
+}
+
 __device__ __forceinline__ double reduce_partials(const double *partials, int64_t n) {
     __shared__ double red[32];
     double s = 0.0;
@@ -165,6 +206,26 @@ __global__ void k_resid_update(const double *partials, int64_t n, DevStatus *st,
         } else if (st->count >= m_max) {
             st->done = 1;
             st->noconv = 1;
+        }
+    }
+}
+
+__global__ void k_cheb_update(const double *partials, int64_t n, DevStatus *st, ChebParams cp, int resid, double tol2,
+                              int m_max) {
+    if (st->done) return;
+    double t = reduce_partials(partials, n);
+    if (threadIdx.x == 0) {
+        const int s = st->count;
+        st->cheb_rho = s == 0 ? 1.0 / cp.sig : 1.0 / (2.0 * cp.sig - st->cheb_rho);
+        st->r2 = t;
+        st->count = s + 1;
+        if (resid) {
+            if (t <= tol2 * st->nrm2) {
+                st->done = 1;
+            } else if (st->count >= m_max) {
+                st->done = 1;
+                st->noconv = 1;
+            }
         }
     }
 }
@@ -263,6 +324,24 @@ int launch_resid_init(double *partials, int64_t nparts, DevStatus *st, cudaStrea
     return 1;
 }
 
+template <typename T>
+int launch_cheb_sweep(const Geo &g, int dims, const Coef<T> &c, const StagedPtrs<T> &p, const ChebParams &cp,
+                      cudaStream_t s) {
+    if (dims == 3)
+        k_cheb_sweep<T, 3><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, c, p, cp);
+    else if (dims == 2)
+        k_cheb_sweep<T, 2><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, c, p, cp);
+    else
+        k_cheb_sweep<T, 1><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, c, p, cp);
+    return 1;
+}
+
+int launch_cheb_update(double *partials, int64_t nparts, DevStatus *st, const ChebParams &cp, bool resid,
+                       double tol2, int m_max, cudaStream_t s) {
+    k_cheb_update<<<1, 1024, 0, s>>>(partials, nparts, st, cp, resid ? 1 : 0, tol2, m_max);
+    return 1;
+}
+
 int launch_resid_update(double *partials, int64_t nparts, DevStatus *st, double tol2, int m_max, cudaStream_t s) {
     k_resid_update<<<1, 1024, 0, s>>>(partials, nparts, st, tol2, m_max);
     return 1;
@@ -298,6 +377,8 @@ int launch_faraday(const Geo &g, int dims, const Coef<T> &c, T *const E[3], T *c
     template int launch_staged_sweep<T>(const Geo &, int, const Coef<T> &, const StagedPtrs<T> &,             \
                                         const T *const[3], T *const[3], bool, cudaStream_t);                  \
     template int launch_resid_sweep<T>(const Geo &, int, const Coef<T> &, const StagedPtrs<T> &, cudaStream_t); \
+    template int launch_cheb_sweep<T>(const Geo &, int, const Coef<T> &, const StagedPtrs<T> &, const ChebParams &, \
+                                      cudaStream_t);                                                         \
     template int launch_update_e<T>(const Geo &, T *const[3], const T *const[3], cudaStream_t);               \
     template int launch_update_e_resid<T>(const Geo &, const StagedPtrs<T> &, cudaStream_t);                  \
     template int launch_faraday<T>(const Geo &, int, const Coef<T> &, T *const[3], T *const[3], cudaStream_t);

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfmx.so")
 # status codes
 FMX_OK, FMX_EINVAL, FMX_ECFL, FMX_ENOCONV, FMX_ECUDA, FMX_ETIMEOUT, FMX_ESTATE, FMX_EUNSUPPORTED = range(8)
 FMX_F32, FMX_F64 = 0, 1
-FMX_ITER_FIXED, FMX_ITER_RESIDUAL = 0, 1
+FMX_ITER_FIXED, FMX_ITER_RESIDUAL, FMX_ITER_CHEB_FIXED, FMX_ITER_CHEB_RESIDUAL = 0, 1, 2, 3
 FMX_FILTER_NONE, FMX_FILTER_CURRENT, FMX_FILTER_FIELDS = 0, 1, 2
 FMX_ENGINE_AUTO, FMX_ENGINE_STAGED, FMX_ENGINE_FUSED = 0, 1, 2
 FMX_HOST, FMX_DEVICE = 0, 1
@@ -95,6 +95,7 @@ def _load():
         "fmx_gauss_accumulate": (ctypes.c_int, [G, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
                                                 ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
         "fmx_gauss_accumulated": (ctypes.c_int, [G, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+        "fmx_cheb_interval": (ctypes.c_int, [G, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
         "fmx_gauss_setup": (ctypes.c_int, [G, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                            ctypes.c_double, ctypes.c_double]),
@@ -150,6 +151,7 @@ fmx_gauss_source = _lib.fmx_gauss_source
 fmx_gauss_project = _lib.fmx_gauss_project
 fmx_gauss_accumulate = _lib.fmx_gauss_accumulate
 fmx_gauss_accumulated = _lib.fmx_gauss_accumulated
+fmx_cheb_interval = _lib.fmx_cheb_interval
 fmx_gauss_setup = _lib.fmx_gauss_setup
 fmx_gauss_run = _lib.fmx_gauss_run
 fmx_gauss_adjoint_run = _lib.fmx_gauss_adjoint_run

@@ -79,3 +79,22 @@ def test_interval_holds_the_grid_spectrum():
                 M[..., i, j] = np.broadcast_to(np.real(A[i][j]), shp)
         w = np.linalg.eigvalsh(M)
         assert w.min() >= lo and w.max() <= hi and hi < 1.0
+
+
+@pytest.mark.parametrize("shape,courant,d", [((64, 64), 0.5, (1.0, 1.0, 1.0)), ((16, 16, 16), 0.5, (1.0, 1.0, 1.0)),
+                                             ((40,), 0.9, (1.0, 1.0, 1.0)), ((20, 12, 8), 0.7, (1.0, 0.8, 1.2))])
+def test_library_interval_matches_oracle(shape, courant, d):
+    """fmx_cheb_interval (the library's own sampling and eigenvalues, host
+    code: no GPU needed) against the oracle's interval."""
+    import ctypes
+    from paper_1907_13088_gb300 import fmx
+    p = fmx.make_params(shape, courant=courant, d=d, iter_mode=fmx.FMX_ITER_CHEB_FIXED, precision=fmx.FMX_F64)
+    h = ctypes.c_void_p()
+    fmx.check(fmx.fmx_create(ctypes.byref(p), ctypes.byref(h), None), "fmx_create")
+    try:
+        lo, hi = ctypes.c_double(), ctypes.c_double()
+        fmx.check(fmx.fmx_cheb_interval(h, ctypes.byref(lo), ctypes.byref(hi)), "fmx_cheb_interval")
+    finally:
+        fmx.fmx_destroy(h)
+    olo, ohi = spectral.a_interval(core.Params(shape=shape, courant=courant, d=d))
+    assert abs(lo.value - olo) < 1e-13 and abs(hi.value - ohi) < 1e-13

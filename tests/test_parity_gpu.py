@@ -142,6 +142,32 @@ def test_3d_march_and_staged_branches(fmx, kw):
     assert_parity(Eg, Bg, Eo, Bo, TOL32, f"3d fp32 {kw}")
 
 
+@pytest.mark.parametrize("shape", [(37, 29), (13, 11, 7), (40,)])
+def test_chebyshev_modes(fmx, shape):
+    """Chebyshev acceleration (staged engine): m sweeps and residual mode, FP64
+    against the oracle's Chebyshev solve; FP32 with the FP32-rounded
+    coefficients; residual mode needs fewer sweeps than Algorithm 1."""
+    E, B, J = _inputs(shape, 91, np.float64)
+    kw = dict(m=5, filter_passes=1, courant=0.8)
+    Eg, Bg, _ = _run_gpu(fmx, shape, E, B, J, 3, precision=1, engine=1, iter_mode=fmx.FMX_ITER_CHEB_FIXED, **kw)
+    Eo, Bo, rc, _ = _oracle(shape, E, B, J, 3, cheb=True, **kw)
+    assert_parity(Eg, Bg, Eo, Bo, TOL64, f"chebyshev fixed fp64 {shape}")
+    E32, B32, J32 = (x.astype(np.float32) for x in (E, B, J))
+    Eg, Bg, _ = _run_gpu(fmx, shape, E32, B32, J32, 3, precision=0, engine=1, iter_mode=fmx.FMX_ITER_CHEB_FIXED, **kw)
+    Eo, Bo, rc, _ = _oracle(shape, E32.astype(np.float64), B32.astype(np.float64), J32.astype(np.float64), 3,
+                            cheb=True, coef_f32=True, **kw)
+    assert_parity(Eg, Bg, Eo, Bo, TOL32, f"chebyshev fixed fp32 {shape}")
+    rk = dict(filter_passes=1, courant=0.8, tol=1e-12, m_max=5000)
+    Eg, Bg, info = _run_gpu(fmx, shape, E, B, J, 3, precision=1, engine=1, iter_mode=fmx.FMX_ITER_CHEB_RESIDUAL, **rk)
+    Eo, Bo, rc, st = _oracle(shape, E, B, J, 3, cheb=True, residual=True, **rk)
+    assert_parity(Eg, Bg, Eo, Bo, TOL64, f"chebyshev residual fp64 {shape}")
+    d_cheb = info["grid"].diagnostics()
+    _, _, info_j = _run_gpu(fmx, shape, E, B, J, 3, precision=1, engine=1, iter_mode=fmx.FMX_ITER_RESIDUAL, **rk)
+    d_jac = info_j["grid"].diagnostics()
+    assert d_cheb["last_sweeps"] == st["last_sweeps"]
+    assert d_cheb["total_sweeps"] < d_jac["total_sweeps"]
+
+
 def test_staged_fields_filter_and_lumped(fmx):
     shape = (24, 18)
     E, B, J = _inputs(shape, 41, np.float64)
