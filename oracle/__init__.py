@@ -7,4 +7,6 @@ never imports it and shares no code with it.
 * ``oracle.core``     -- ctypes front end of the stencil oracle (plain C).
 * ``oracle.spectral`` -- per-wavevector form of the same step and the paper's
                          closed forms (dispersion, CFL, phase speed).
+* ``oracle.nci``      -- NCI resonance curves and asymptotic growth rate
+                         (Sec. 3, App. E).
 """
