@@ -357,6 +357,56 @@ typedef struct {
 fmx_status fmx_profile_enable(fmx_grid *g, int enable);
 fmx_status fmx_profile_read(fmx_grid *g, fmx_kernel_stat *out, int max, int *n);
 
+/* ---------------------------------------------------------------------
+ * NCI closed-form tools (Sec. 3, App. E).  For a cold beam drifting along x
+ * at v -> c on a 2D grid (dx, dy) with dt = courant * dt_CFL,
+ * dt_CFL = 1 / (c sqrt(1/dx^2 + 1/dy^2)) (2D form of Eq. dt_cfl_3d):
+ *   - the resonance curves of Eqs. reson1 and reson2: for every alias
+ *     nu = -nu_max..nu_max (Eq. aliasing_x) and every sample k_x, the k_y >= 0
+ *     where the beam line omega = c (k_x + 2 pi nu / dx) meets the EM mode
+ *     (the mirror -k_y is implied; the trivial meeting at omega = k = 0 is
+ *     not a crossing).  The beam is taken without time aliasing
+ *     and only where |omega dt| <= pi, the zone of the EM branch: the reading
+ *     under which the curves show what Sec. 4.2 states (nu = 0 only for
+ *     dt > dt_CFL / sqrt 2, no |nu| >= 2, |k_x| > 2.06 / dx);
+ *   - the asymptotic growth rate Gamma of Eq. NCI-growth-rate at each crossing,
+ *     with the momentum-conserving interpolation factors of Sec. 3 for a
+ *     B-spline particle shape of order shape_order;
+ *   - the fastest-growing mode over all crossings.
+ * Computed in FP64 on the device. */
+#define FMX_NCI_MAX_SHAPE_ORDER 16
+#define FMX_NCI_MAX_ALIAS 64
+#define FMX_NCI_MAX_KX (1 << 26)
+
+typedef struct {
+    double dx, dy;     /* cell sizes (> 0)                                       */
+    double c;          /* light speed (> 0)                                      */
+    double courant;    /* dt / dt_CFL, in (0, 1]                                 */
+    double omega_p;    /* relativistic plasma frequency of the beam (>= 0)       */
+    int shape_order;   /* B-spline order l of the particle shape, 0..16          */
+    int nu_max;        /* aliases nu = -nu_max..nu_max, 0..64                    */
+    int nkx;           /* k_x samples, 1..2^26                                   */
+} fmx_nci_params;
+
+/* fmx_nci_resonance -- the k_x samples are the cell centres of the first
+ * zone, k_x,i = (2 i + 1 - nkx) pi / (nkx dx), i = 0..nkx-1.
+ *   kx    : device double[nkx] receiving those samples, or NULL;
+ *   ky    : device double[(2 nu_max + 1) * nkx], row r = nu + nu_max: the
+ *           crossing k_y in [0, pi/dy], NaN where the curve of that nu does
+ *           not cross that k_x;
+ *   gamma : same layout, Gamma at the crossing, 0 where there is none;
+ *   best  : device double[4] receiving (Gamma_max, k_x, k_y, nu) of the
+ *           fastest-growing crossing (the lowest flat index among equal
+ *           maxima), or (0, NaN, NaN, NaN) when nothing crosses; NULL skips
+ *           the search.  Its first two words are also the search's working
+ *           storage while the call's work runs.
+ *   stream: cudaStream_t the work is enqueued on (NULL: legacy stream);
+ *           asynchronous, nothing is allocated.
+ * Caller-owned buffers, 8-byte aligned.  Errors: FMX_EINVAL (a parameter out
+ * of range, ky or gamma NULL), FMX_ECUDA (a launch failed). */
+fmx_status fmx_nci_resonance(const fmx_nci_params *p, double *kx, double *ky, double *gamma, double *best,
+                             void *stream);
+
 /* Size of the device scratch array behind fmx_step_static (4 MiB). */
 #define FMX_STATIC_SCRATCH_BYTES (4u << 20)
 

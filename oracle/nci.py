@@ -31,6 +31,8 @@ Readings (the paper is terse here):
 * [k]_x, alpha_x are the grid symbols of k_x in the first zone; the shape
   factors s_{l,x} take the aliased k_x' ("dummy variables with aliasing
   wavevector"); nu_y = 0, so k_y' = k_y.
+* The beam and the EM mode also meet trivially at k = 0, omega = 0 (the
+  uniform static field, where Gamma is 0/0); that point is not a crossing.
 * The resonance is solved for k_y >= 0 at each k_x (its mirror -k_y has the
   same Gamma): f(k_y) = [omega]^2/(alpha_t c^2) - [k_x]^2/alpha_x
   - [k_y]^2/alpha_y decreases on [0, pi/dy], so there is at most one root,
@@ -66,9 +68,9 @@ def _alpha(k, d):
 
 def beam_frequency(kxp, dt, c=1.0):
     """omega = c k_x' (Eq. reson2 with mu = 0) and whether it lies in the
-    zone of the EM branch, |omega dt| <= pi."""
+    zone of the EM branch, |omega dt| <= pi, away from the trivial omega = 0."""
     om = c * kxp
-    return om, np.abs(om * dt) <= math.pi
+    return om, (np.abs(om * dt) <= math.pi) & (om != 0.0)
 
 
 def xi(omega, dt):

@@ -51,6 +51,12 @@ class fmx_kernel_stat(ctypes.Structure):
                 ("bytes_per_launch", ctypes.c_double)]
 
 
+class fmx_nci_params(ctypes.Structure):
+    _fields_ = [("dx", ctypes.c_double), ("dy", ctypes.c_double), ("c", ctypes.c_double),
+                ("courant", ctypes.c_double), ("omega_p", ctypes.c_double), ("shape_order", ctypes.c_int),
+                ("nu_max", ctypes.c_int), ("nkx", ctypes.c_int)]
+
+
 class fmx_diag(ctypes.Structure):
     _fields_ = [("w_scheme", ctypes.c_double), ("w_plain", ctypes.c_double), ("divb_max", ctypes.c_double),
                 ("divb_l2", ctypes.c_double), ("gauss_max", ctypes.c_double), ("gauss_l2", ctypes.c_double),
@@ -115,6 +121,8 @@ def _load():
         "fmx_batch_destroy": (None, [G]),
         "fmx_profile_read": (ctypes.c_int, [G, ctypes.POINTER(fmx_kernel_stat), ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_int)]),
+        "fmx_nci_resonance": (ctypes.c_int, [ctypes.POINTER(fmx_nci_params), ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -167,6 +175,7 @@ fmx_batch_items = _lib.fmx_batch_items
 fmx_batch_launch_count = _lib.fmx_batch_launch_count
 fmx_batch_destroy = _lib.fmx_batch_destroy
 fmx_profile_read = _lib.fmx_profile_read
+fmx_nci_resonance = _lib.fmx_nci_resonance
 FMX_STATIC_SCRATCH_BYTES = 4 << 20
 
 
@@ -501,3 +510,32 @@ class Batch:
     @property
     def launches(self) -> int:
         return int(fmx_batch_launch_count(self.handle))
+
+
+def nci_params(dx=1.0, dy=1.0, c=1.0, courant=0.5, omega_p=1.0 / 16.0, shape_order=1, nu_max=1, nkx=4096):
+    p = fmx_nci_params()
+    p.dx, p.dy, p.c, p.courant, p.omega_p = float(dx), float(dy), float(c), float(courant), float(omega_p)
+    p.shape_order, p.nu_max, p.nkx = int(shape_order), int(nu_max), int(nkx)
+    return p
+
+
+def nci_resonance(device="cuda", stream=None, **kw):
+    """fmx_nci_resonance on torch buffers: returns dict kx [nkx], ky and gamma
+    [2 nu_max + 1, nkx] (device tensors, FP64), best = (Gamma_max, k_x, k_y,
+    nu) and nus.  Keyword arguments as ``nci_params``; enqueued on
+    ``stream`` (default: torch's current stream) and synchronised."""
+    import torch
+
+    p = nci_params(**kw)
+    dev = torch.device(device)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    rows = 2 * p.nu_max + 1
+    kx = torch.empty(p.nkx, dtype=torch.float64, device=dev)
+    ky = torch.empty((rows, p.nkx), dtype=torch.float64, device=dev)
+    gamma = torch.empty((rows, p.nkx), dtype=torch.float64, device=dev)
+    best = torch.empty(4, dtype=torch.float64, device=dev)
+    check(fmx_nci_resonance(ctypes.byref(p), kx.data_ptr(), ky.data_ptr(), gamma.data_ptr(), best.data_ptr(),
+                            ctypes.c_void_p(stream.cuda_stream)), "fmx_nci_resonance")
+    stream.synchronize()
+    return dict(kx=kx, ky=ky, gamma=gamma, best=tuple(best.tolist()), nus=list(range(-p.nu_max, p.nu_max + 1)))

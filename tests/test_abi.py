@@ -127,3 +127,22 @@ def test_batch_validation(fmx):
     assert fmx.fmx_batch_create((fmx.fmx_params * 1)(*cfl), 1, ctypes.byref(h)) == fmx.FMX_ECFL
     f64 = [fmx.make_params((64, 40), precision=1, stream=stream)]
     assert fmx.fmx_batch_create((fmx.fmx_params * 1)(*f64), 1, ctypes.byref(h)) == fmx.FMX_EINVAL
+
+
+def test_nci_rejects_bad_parameters_before_any_device_work(fmx):
+    """fmx_nci_resonance validates on the host and returns FMX_EINVAL before it
+    enqueues anything (the output pointers are never touched here; the test
+    only runs where there is no GPU)."""
+    import ctypes
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("host-only check")
+    for bad in (dict(courant=0.0), dict(courant=1.01), dict(dx=-1.0), dict(dy=float("inf")), dict(c=0.0),
+                dict(nkx=0), dict(nkx=(1 << 26) + 1), dict(nu_max=-1), dict(nu_max=65), dict(shape_order=-1),
+                dict(shape_order=17), dict(omega_p=float("nan")), dict(omega_p=-1.0)):
+        p = fmx.nci_params(**bad)
+        assert fmx.fmx_nci_resonance(ctypes.byref(p), None, 16, 16, None, None) == fmx.FMX_EINVAL, bad
+        assert b"fmx_nci_resonance" in fmx.fmx_last_error()
+    p = fmx.nci_params()
+    assert fmx.fmx_nci_resonance(ctypes.byref(p), None, None, 16, None, None) == fmx.FMX_EINVAL
+    assert fmx.fmx_nci_resonance(None, None, 16, 16, None, None) == fmx.FMX_EINVAL

@@ -160,8 +160,17 @@ def test_resonance_table_and_best():
     assert abs(nci.growth_rate(kx, ky, int(nu), DX, DY, r["dt"], WP, 1) - g) == 0.0
 
 
+def test_origin_is_not_a_crossing():
+    """Odd nkx samples k_x = 0, where the nu = 0 beam meets the EM mode only
+    at omega = k = 0."""
+    r = nci.resonance(1025, 0.9, DX, DY, WP, 1, nu_max=1)
+    assert r["kx"][512] == 0.0
+    assert np.isnan(r["ky"][1, 512]) and r["gamma"][1, 512] == 0.0
+    assert np.all(np.isfinite(r["gamma"])) and np.isfinite(r["best"][0])
+
+
 MUTANTS = {
-    "time_aliased_beam": ("return om, np.abs(om * dt) <= math.pi", "return om, np.abs(om * dt) >= 0.0"),
+    "time_aliased_beam": ("(np.abs(om * dt) <= math.pi)", "(np.abs(om * dt) >= 0.0)"),
     "reson_without_alpha_t": ("return x0 ** 2 / (x2 * c * c) - _bracket(kx, dx)",
                               "return x0 ** 2 / (c * c) - _bracket(kx, dx)"),
     "xi1_sign": ("x1 = np.cos(omega * dt / 2.0)", "x1 = -np.cos(omega * dt / 2.0)"),
