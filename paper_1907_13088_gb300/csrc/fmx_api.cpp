@@ -398,14 +398,24 @@ fmx_status staged_step(fmx_grid *g) {
     if (mode == FMX_ITER_FIXED) {
         const T *in[3] = {P.dEp[0], P.dEp[1], P.dEp[2]};
         const T *dp[3] = {P.dEp[0], P.dEp[1], P.dEp[2]};
+        bool updated = false;
         for (int it = 0; it < g->p.m; ++it) {
+            // the z-marching FP32 sweep can apply E^{n+1} = E^n + dE in its last pass
+            if (march && it == g->p.m - 1) {
+                const int n = fmx::launch_march3d_sweep<T>(g->geo, c, dp, in, P.E, g->stream, true);
+                g->launches += n;
+                if (n) {
+                    updated = true;
+                    break;
+                }
+            }
             T *out[3];
             for (int q = 0; q < 3; ++q) out[q] = (it % 2 == 0) ? P.dEa[q] : P.dEb[q];
             g->launches += march ? fmx::launch_march3d_sweep<T>(g->geo, c, dp, in, out, g->stream)
                                  : fmx::launch_staged_sweep<T>(g->geo, g->p.dims, c, P, in, out, false, g->stream);
             for (int q = 0; q < 3; ++q) in[q] = out[q];
         }
-        g->launches += fmx::launch_update_e<T>(g->geo, P.E, in, g->stream);
+        if (!updated) g->launches += fmx::launch_update_e<T>(g->geo, P.E, in, g->stream);
         g->last_sweeps = g->p.m;
         g->total_sweeps += g->p.m;
     } else {

@@ -106,7 +106,7 @@ int launch_march3d_source(const Geo &g, const Coef<T> &c, const T *const B[3], c
                           T *const out[3], cudaStream_t s);
 template <typename T>
 int launch_march3d_sweep(const Geo &g, const Coef<T> &c, const T *const dEp[3], const T *const in[3], T *const out[3],
-                         cudaStream_t s);
+                         cudaStream_t s, bool update = false);
 
 // Diagnostics (diag.cu): writes 6 FP64 values to out_dev (w_scheme sum,
 // w_plain sum, divb max, divb sum sq, gauss max, gauss sum sq).

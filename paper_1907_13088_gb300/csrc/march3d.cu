@@ -1,16 +1,22 @@
 // 3D z-marching kernels for the source (with the one-pass current filter) and
 // the sweeps of Algorithm 1.  A CTA owns a TX x TY column tile and walks a
 // segment of z planes; each input plane of the tile, with a one-cell halo in
-// x and y, is loaded once into a 4-slot shared-memory ring, so that every
-// stencil of the step (the A operator of Eqs. matrixA_1st..matrixA_last, the
-// averaged curl of Eqs. ampere_aux_x..z, the 27-point binomial) reads its
-// neighbours from shared memory.  One __syncthreads per plane: plane k+1 goes
-// into slot (k+1) & 3 while slots (k-1..k+1) & 3 are read for plane k, and the
-// slot written next, (k+2) & 3, is none of them.  The stencil arithmetic is
+// x and y, is copied once into a shared-memory ring, so that every stencil of
+// the step (the A operator of Eqs. matrixA_1st..matrixA_last, the averaged
+// curl of Eqs. ampere_aux_x..z, the 27-point binomial) reads its neighbours
+// from shared memory.  The planes travel by cp.async, several planes ahead
+// of the one being computed, so no register holds data in flight: planes
+// k-1..k+1 are read while planes k+2..k+RS-2 are on their way (RS ring
+// slots), and the sweep's dE' of the thread's own cell rides in a second ring
+// of the same depth.  One __syncthreads per plane; the slot refilled after it
+// was last read in the previous plane's iteration.  The stencil arithmetic is
 // the staged engine's (stencil.cuh), read through a ring accessor.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "fmx_internal.h"
+#include "pair2.cuh"
 #include "stencil.cuh"
 
 namespace fmx {
@@ -19,6 +25,13 @@ namespace {
 constexpr int TX = 32, TY = 8, NTH = TX * TY;  // tile and threads
 constexpr int RW = TX + 2, RH = TY + 2, PL = RW * RH;  // a tile plane with its halo
 constexpr int ZSEG = 32;                                // planes per CTA
+
+// ring slots: 8 for FP32 (five planes in flight), 4 for FP64 (one)
+template <typename T>
+struct RingDepth {
+    static constexpr int RS = sizeof(T) == 4 ? 8 : 4;
+    static constexpr int LA = RS - 3;  // copy groups in flight ahead of the plane computed
+};
 
 // component c of the ring at a shift (dx, dy in [-1, 1], dz in [-1, 1]) of
 // the thread's cell in plane k
@@ -35,17 +48,34 @@ struct Ring {
 
 __device__ __forceinline__ int wrapm(int v, int n) { return ((v % n) + n) % n; }
 
-// Loads of the tile's planes with their halo: a thread owns cells q = tid and
+// one element, global -> shared, asynchronous (cp.async, 4 or 8 bytes)
+template <typename T>
+__device__ __forceinline__ void cp_async_el(T *dst, const T *src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_pair(float *dst, const float *src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Copies of the tile's planes with their halo: a thread owns cells q = tid and
 // q = tid + NTH (when < PL) of every plane; their in-plane offsets are fixed,
-// so they are computed once.  fetch(k) reads plane k (periodic) of the N
-// components into registers, commit(slot) stores them into the ring; the
-// loop fetches plane k+2 while it computes plane k.
-template <typename T, int N>
-struct PlaneLoader {
+// so they are computed once.  issue(k) starts the copy of plane k (periodic)
+// of the N components into ring slot k mod RS.
+template <typename T, int N, int RS>
+struct AsyncPlanes {
     const T *src[N];
     int off0, off1;  // in-plane offsets of the thread's cells (off1 < 0: none)
     int q0, q1;
-    T v0[N], v1[N];
     __device__ __forceinline__ void init(const T *const s[N], const Geo &g, int x0, int y0) {
 #pragma unroll
         for (int c = 0; c < N; ++c) src[c] = s[c];
@@ -59,32 +89,26 @@ struct PlaneLoader {
         off0 = off(q0);
         off1 = q1 >= 0 ? off(q1) : -1;
     }
-    __device__ __forceinline__ void fetch(const Geo &g, int k) {
+    __device__ __forceinline__ void issue(T *ring, const Geo &g, int k) const {
         const int64_t base = (int64_t)wrapm(k, g.nz) * g.plane;
+        const int slot = k & (RS - 1);
 #pragma unroll
         for (int c = 0; c < N; ++c) {
-            v0[c] = src[c][base + off0];
-            if (q1 >= 0) v1[c] = src[c][base + off1];
-        }
-    }
-    __device__ __forceinline__ void commit(T *ring, int slot) const {
-#pragma unroll
-        for (int c = 0; c < N; ++c) {
-            ring[(slot * N + c) * PL + q0] = v0[c];
-            if (q1 >= 0) ring[(slot * N + c) * PL + q1] = v1[c];
+            cp_async_el(ring + (slot * N + c) * PL + q0, src[c] + base + off0);
+            if (q1 >= 0) cp_async_el(ring + (slot * N + c) * PL + q1, src[c] + base + off1);
         }
     }
 };
 
-template <typename T, int N>
+template <typename T, int N, int RS>
 __device__ __forceinline__ void ring_fields(Ring<T> f[N], const T *ring, int k) {
     const int cell = (threadIdx.y + 1) * RW + threadIdx.x + 1;
 #pragma unroll
     for (int c = 0; c < N; ++c) {
         f[c].base = ring + c * PL;
-        f[c].sm1 = ((k - 1) & 3) * N * PL;
-        f[c].s0 = (k & 3) * N * PL;
-        f[c].sp1 = ((k + 1) & 3) * N * PL;
+        f[c].sm1 = ((k - 1) & (RS - 1)) * N * PL;
+        f[c].s0 = (k & (RS - 1)) * N * PL;
+        f[c].sp1 = ((k + 1) & (RS - 1)) * N * PL;
         f[c].cell = cell;
     }
 }
@@ -95,36 +119,57 @@ __device__ __forceinline__ void ring_fields(Ring<T> f[N], const T *ring, int k) 
 template <typename T>
 __global__ void __launch_bounds__(NTH) k3_sweep(Geo g, Coef<T> c, const T *p0, const T *p1, const T *p2,
                                                 const T *i0, const T *i1, const T *i2, T *o0, T *o1, T *o2) {
+    constexpr int RS = RingDepth<T>::RS, LA = RingDepth<T>::LA;
     extern __shared__ __align__(16) unsigned char m3raw[];
-    T *ring = reinterpret_cast<T *>(m3raw);  // [4][3][PL]
+    T *ring = reinterpret_cast<T *>(m3raw);  // [RS][3][PL] input planes with halo
+    T *own = ring + RS * 3 * PL;             // [RS][3][NTH] dE' of each thread's cell
     const T *in[3] = {i0, i1, i2};
+    const T *dp[3] = {p0, p1, p2};
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * ZSEG, z1 = min(z0 + ZSEG, g.nz);
-    PlaneLoader<T, 3> ld;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    AsyncPlanes<T, 3, RS> ld;
     ld.init(in, g, x0, y0);
-    ld.fetch(g, z0 - 1);
-    ld.commit(ring, (z0 - 1) & 3);
-    ld.fetch(g, z0);
-    ld.commit(ring, z0 & 3);
-    ld.fetch(g, z0 + 1);
     Pos p;
     p.i = x0 + threadIdx.x;
     p.j = y0 + threadIdx.y;
     const bool inside = p.i < g.nx && p.j < g.ny;
+    const int64_t cell = (int64_t)p.j * g.pitch + p.i;
+    // copy group m: input plane z0+1+m and dE' plane z0+m (group 0 also planes
+    // z0-1 and z0); planes past the segment are not copied (empty groups keep
+    // the count)
+    auto issue = [&](int m) {
+        if (m == 0) {
+            ld.issue(ring, g, z0 - 1);
+            ld.issue(ring, g, z0);
+        }
+        if (z0 + 1 + m <= z1) ld.issue(ring, g, z0 + 1 + m);
+        const int kd = z0 + m;
+        if (inside && kd < z1) {
+            const int slot = kd & (RS - 1);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) cp_async_el(own + (slot * 3 + q) * NTH + tid, dp[q] + (int64_t)kd * g.plane + cell);
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int m = 0; m < LA; ++m) issue(m);
     for (int k = z0; k < z1; ++k) {
-        ld.commit(ring, (k + 1) & 3);
-        if (k + 1 < z1) ld.fetch(g, k + 2);
-        __syncthreads();
+        cp_async_wait<LA - 1>();  // this thread's copies of group k - z0
+        __syncthreads();          // everyone's, and every read of the slots refilled next is done
+        issue(k - z0 + LA);
         if (inside) {
             p.k = k;
             Ring<T> f[3];
-            ring_fields<T, 3>(f, ring, k);
-            const int64_t idx = (int64_t)k * g.plane + (int64_t)p.j * g.pitch + p.i;
-            o0[idx] = p0[idx] + apply_a<T, 3, 0>(f, p, c);
-            o1[idx] = p1[idx] + apply_a<T, 3, 1>(f, p, c);
-            o2[idx] = p2[idx] + apply_a<T, 3, 2>(f, p, c);
+            ring_fields<T, 3, RS>(f, ring, k);
+            const T *d = own + (k & (RS - 1)) * 3 * NTH + tid;
+            const int64_t idx = (int64_t)k * g.plane + cell;
+            o0[idx] = d[0] + apply_a<T, 3, 0>(f, p, c);
+            o1[idx] = d[NTH] + apply_a<T, 3, 1>(f, p, c);
+            o2[idx] = d[2 * NTH] + apply_a<T, 3, 2>(f, p, c);
         }
     }
+    cp_async_wait<0>();
 }
 
 // dE' = C_b (alpha B) - q F j, 3D, F = one (1/4, 1/2, 1/4) pass along each
@@ -133,30 +178,37 @@ template <typename T, int PASSES, bool HJ>
 __global__ void __launch_bounds__(NTH) k3_source(Geo g, Coef<T> c, const T *b0, const T *b1, const T *b2,
                                                  const T *j0, const T *j1, const T *j2, T *o0, T *o1, T *o2) {
     constexpr int N = HJ ? 6 : 3;
+    constexpr int RS = RingDepth<T>::RS, LA = RingDepth<T>::LA;
     extern __shared__ __align__(16) unsigned char m3raw[];
-    T *ring = reinterpret_cast<T *>(m3raw);  // [4][N][PL]
+    T *ring = reinterpret_cast<T *>(m3raw);  // [RS][N][PL]
     const T *src[6] = {b0, b1, b2, j0, j1, j2};
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * ZSEG, z1 = min(z0 + ZSEG, g.nz);
-    PlaneLoader<T, N> ld;
+    AsyncPlanes<T, N, RS> ld;
     ld.init(src, g, x0, y0);
-    ld.fetch(g, z0 - 1);
-    ld.commit(ring, (z0 - 1) & 3);
-    ld.fetch(g, z0);
-    ld.commit(ring, z0 & 3);
-    ld.fetch(g, z0 + 1);
+    // copy group m: plane z0+1+m (group 0 also planes z0-1 and z0)
+    auto issue = [&](int m) {
+        if (m == 0) {
+            ld.issue(ring, g, z0 - 1);
+            ld.issue(ring, g, z0);
+        }
+        if (z0 + 1 + m <= z1) ld.issue(ring, g, z0 + 1 + m);
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int m = 0; m < LA; ++m) issue(m);
     Pos p;
     p.i = x0 + threadIdx.x;
     p.j = y0 + threadIdx.y;
     const bool inside = p.i < g.nx && p.j < g.ny;
     for (int k = z0; k < z1; ++k) {
-        ld.commit(ring, (k + 1) & 3);
-        if (k + 1 < z1) ld.fetch(g, k + 2);
+        cp_async_wait<LA - 1>();
         __syncthreads();
+        issue(k - z0 + LA);
         if (inside) {
             p.k = k;
             Ring<T> f[N];
-            ring_fields<T, N>(f, ring, k);
+            ring_fields<T, N, RS>(f, ring, k);
             T d[3] = {curl_alpha_b<T, 3, 0>(f, p, c), curl_alpha_b<T, 3, 1>(f, p, c), curl_alpha_b<T, 3, 2>(f, p, c)};
             if constexpr (HJ) {
 #pragma unroll
@@ -186,6 +238,292 @@ __global__ void __launch_bounds__(NTH) k3_source(Geo g, Coef<T> c, const T *b0, 
             o2[idx] = d[2];
         }
     }
+    cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
+// FP32 sweep, two adjacent columns per thread (even n_x).  The tile is 64
+// columns x 8 rows; a smem row holds column x0 + j at index j + 2 (j = -1..64),
+// so a thread's own pair sits at an even index and is one 8-byte load, and its
+// x-neighbours (columns 2t-1 and 2t+2) are single loads.  The A operator is
+// evaluated on column pairs with packed FP32x2 arithmetic.  The planes arrive
+// by cp.async like the scalar kernel's (8-byte copies of column pairs, 4-byte
+// copies of the two halo columns); dE' of the thread's own pair is prefetched
+// into registers two planes ahead (E^n, when the sweep also applies the update
+// E^{n+1} = E^n + dE, is loaded as the plane's work starts).
+using pair2::f2;
+constexpr int TXP = 32, TX2 = 2 * TXP;              // threads along x, columns of the tile
+constexpr int RW2 = TX2 + 4, PL2 = RW2 * RH;         // smem row and plane (one component)
+constexpr int NPC = TXP * RH, NCP2 = NPC + 2 * RH;  // pair copies and halo copies per plane
+
+struct Coef3P {
+    f2 ax, ay, az, ayz, azx, axy, byz, bzx, bxy, c6, kx, ky, kz, q;
+};
+template <int AX>
+__device__ __forceinline__ f2 ck(const Coef3P &c) {
+    return AX == 0 ? c.kx : (AX == 1 ? c.ky : c.kz);
+}
+
+template <int AX>
+__device__ __forceinline__ f2 cdiag(const Coef3P &c) {
+    return AX == 0 ? c.ax : (AX == 1 ? c.ay : c.az);
+}
+template <int AX>
+__device__ __forceinline__ f2 cpair(const Coef3P &c) {
+    return AX == 0 ? c.ayz : (AX == 1 ? c.azx : c.axy);
+}
+template <int THIRD>
+__device__ __forceinline__ f2 ccross(const Coef3P &c) {
+    return THIRD == 0 ? c.byz : (THIRD == 1 ? c.bzx : c.bxy);
+}
+
+// Dbar_{ax ax} of component q at offset (ox, oy, oz), on pairs
+template <int Q, int AX, typename F>
+__device__ __forceinline__ f2 d2p(const F &V, int ox, int oy, int oz) {
+    constexpr int ex = AX == 0, ey = AX == 1, ez = AX == 2;
+    return pair2::fma(V(Q, ox, oy, oz), pair2::m2(), pair2::add(V(Q, ox + ex, oy + ey, oz + ez), V(Q, ox - ex, oy - ey, oz - ez)));
+}
+
+// (A dE)_A on a column pair: the operator of apply_a (stencil.cuh) in 3D
+template <int A, typename F>
+__device__ __forceinline__ f2 apply_a2(const F &V, const Coef3P &c) {
+    using namespace pair2;
+    constexpr int B = (A + 1) % 3, C = (A + 2) % 3;
+    constexpr int bx = B == 0, by = B == 1, bz = B == 2, cx = C == 0, cy = C == 1, cz = C == 2;
+    const f2 dB = d2p<A, B>(V, 0, 0, 0);
+    f2 r = mul(cdiag<B>(c), dB);
+    r = fma(cdiag<C>(c), d2p<A, C>(V, 0, 0, 0), r);
+    const f2 dd = fma(dB, m2(), add(d2p<A, B>(V, cx, cy, cz), d2p<A, B>(V, -cx, -cy, -cz)));
+    r = fma(cpair<A>(c), dd, r);
+    // A_AB E_B with weight (1 + Dbar_CC / 6) at (o_A, o_B) = (1,0), (1,-1), (0,0), (0,-1)
+    auto wb = [&](int oa, int ob) {
+        const int ox = (A == 0) * oa + bx * ob, oy = (A == 1) * oa + by * ob, oz = (A == 2) * oa + bz * ob;
+        return fma(c.c6, d2p<B, C>(V, ox, oy, oz), V(B, ox, oy, oz));
+    };
+    r = fma(ccross<C>(c), fma(add(wb(1, -1), wb(0, 0)), m1(), add(wb(1, 0), wb(0, -1))), r);
+    // A_AC E_C with weight (1 + Dbar_BB / 6) at (o_A, o_C) = (1,0), (1,-1), (0,0), (0,-1)
+    auto wc = [&](int oa, int oc) {
+        const int ox = (A == 0) * oa + cx * oc, oy = (A == 1) * oa + cy * oc, oz = (A == 2) * oa + cz * oc;
+        return fma(c.c6, d2p<C, B>(V, ox, oy, oz), V(C, ox, oy, oz));
+    };
+    r = fma(ccross<B>(c), fma(add(wc(1, -1), wc(0, 0)), m1(), add(wc(1, 0), wc(0, -1))), r);
+    return r;
+}
+
+// a thread's (at most two) copy items of a component plane
+struct PairCopies {
+    int s[2], o[2];  // smem index within a component plane (-1: none), global in-plane offset
+    bool w[2];       // column pair (8 bytes) or halo column (4 bytes)
+    __device__ __forceinline__ void init(const Geo &g, int x0, int y0) {
+        const int tid = threadIdx.y * TXP + threadIdx.x;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int q = tid + r * NTH;
+            s[r] = -1;
+            o[r] = 0;
+            w[r] = false;
+            if (q < NCP2) {
+                int row, j;
+                if (q < NPC) {
+                    row = q / TXP;
+                    j = 2 * (q % TXP);
+                    w[r] = true;
+                } else {
+                    const int h = q - NPC;
+                    row = h / 2;
+                    j = (h & 1) ? TX2 : -1;
+                }
+                const int x = wrapm(x0 + j, g.nx), y = wrapm(y0 - 1 + row, g.ny);
+                s[r] = row * RW2 + 2 + j;
+                o[r] = y * (int)g.pitch + x;
+            }
+        }
+    }
+    template <int RS, int N = 3>
+    __device__ __forceinline__ void issue(float *ring, const float *const src[N], const Geo &g, int k) const {
+        const int64_t base = (int64_t)wrapm(k, g.nz) * g.plane;
+        const int slot = k & (RS - 1);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            if (s[r] < 0) continue;
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                float *dst = ring + (slot * N + c) * PL2 + s[r];
+                const float *sp = src[c] + base + o[r];
+                if (w[r]) cp_async_pair(dst, sp);
+                else cp_async_el(dst, sp);
+            }
+        }
+    }
+};
+
+// out = dEp + A in, or with UPD: E = E + dEp + A in (the last sweep and the
+// update of the step in one pass; E in place)
+template <bool UPD>
+__global__ void __launch_bounds__(NTH, 2) k3_sweep2(Geo g, Coef3P c, const float *p0, const float *p1,
+                                                   const float *p2, const float *i0, const float *i1, const float *i2,
+                                                   float *o0, float *o1, float *o2) {
+    using namespace pair2;
+    constexpr int RS = RingDepth<float>::RS, LA = RingDepth<float>::LA;
+    extern __shared__ __align__(16) unsigned char m3raw[];
+    float *ring = reinterpret_cast<float *>(m3raw);  // [RS][3][PL2]
+    const float *in[3] = {i0, i1, i2};
+    const float *dp[3] = {p0, p1, p2};
+    float *out[3] = {o0, o1, o2};
+    const int x0 = blockIdx.x * TX2, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * ZSEG, z1 = min(z0 + ZSEG, g.nz);
+    PairCopies cp;
+    cp.init(g, x0, y0);
+    const int px = x0 + 2 * threadIdx.x, py = y0 + threadIdx.y;
+    const bool inside = px < g.nx && py < g.ny;
+    const int64_t cell = (int64_t)py * g.pitch + px;
+    const int c0 = (threadIdx.y + 1) * RW2 + 2 + 2 * threadIdx.x;
+    auto issue = [&](int m) {
+        if (m == 0) {
+            cp.issue<RS>(ring, in, g, z0 - 1);
+            cp.issue<RS>(ring, in, g, z0);
+        }
+        if (z0 + 1 + m <= z1) cp.issue<RS>(ring, in, g, z0 + 1 + m);
+        cp_async_commit();
+    };
+    // dE' of the own pair, planes k and k+1: two register buffers
+    f2 pd[2][3];
+    auto ldown = [&](int k, int b) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            pd[b][q] = mk(0.f, 0.f);
+            if (inside && k < z1) pd[b][q] = __ldg(reinterpret_cast<const float2 *>(dp[q] + (int64_t)k * g.plane + cell));
+        }
+    };
+#pragma unroll
+    for (int m = 0; m < LA; ++m) issue(m);
+    ldown(z0, 0);
+    ldown(z0 + 1, 1);
+    auto step = [&](int k, auto bsel) {
+        constexpr int b = decltype(bsel)::value;
+        cp_async_wait<LA - 1>();
+        __syncthreads();
+        issue(k - z0 + LA);
+        f2 d[3], e[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            d[q] = pd[b][q];
+            // E^n of the own pair (UPD), loaded before the stencil work that hides it
+            e[q] = (UPD && inside) ? *reinterpret_cast<const float2 *>(out[q] + (int64_t)k * g.plane + cell) : mk(0.f, 0.f);
+        }
+        ldown(k + 2, b);
+        if (inside) {
+            const int sm1 = ((k - 1) & (RS - 1)) * 3 * PL2, s0 = (k & (RS - 1)) * 3 * PL2,
+                      sp1 = ((k + 1) & (RS - 1)) * 3 * PL2;
+            auto V = [&](int q, int dx, int dy, int dz) -> f2 {
+                const float *row = ring + (dz < 0 ? sm1 : (dz > 0 ? sp1 : s0)) + q * PL2 + c0 + dy * RW2;
+                const f2 pr = *reinterpret_cast<const float2 *>(row);
+                return dx == 0 ? pr : (dx > 0 ? mk(pr.y, row[2]) : mk(row[-1], pr.x));
+            };
+            f2 r[3] = {add(d[0], apply_a2<0>(V, c)), add(d[1], apply_a2<1>(V, c)), add(d[2], apply_a2<2>(V, c))};
+            const int64_t idx = (int64_t)k * g.plane + cell;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                if (UPD) r[q] = add(e[q], r[q]);
+                *reinterpret_cast<float2 *>(out[q] + idx) = r[q];
+            }
+        }
+    };
+    for (int k = z0; k < z1; k += 2) {
+        step(k, std::integral_constant<int, 0>());
+        if (k + 1 < z1) step(k + 1, std::integral_constant<int, 1>());
+    }
+    cp_async_wait<0>();
+}
+
+// dE' = C_b (alpha B) - q F j on a column pair (the source of k3_source,
+// curl_alpha_b in stencil.cuh), 3D; F = one (1/4, 1/2, 1/4) pass along each
+// axis (PASSES = 1) or none.  Ring: B (and j) planes of the 64 x 8 tile,
+// RS slots.
+template <int A, typename F>
+__device__ __forceinline__ f2 curl_alpha_b2(const F &V, const Coef3P &c) {
+    using namespace pair2;
+    constexpr int B = (A + 1) % 3, C = (A + 2) % 3;
+    constexpr int bx = B == 0, by = B == 1, bz = B == 2, cx = C == 0, cy = C == 1, cz = C == 2;
+    // k_B Dbar_B(alpha_C B_C), backward along B
+    const f2 v0 = fma(c.c6, d2p<C, C>(V, 0, 0, 0), V(C, 0, 0, 0));
+    const f2 v1 = fma(c.c6, d2p<C, C>(V, -bx, -by, -bz), V(C, -bx, -by, -bz));
+    f2 r = mul(ck<B>(c), fma(v1, m1(), v0));
+    // - k_C Dbar_C(alpha_B B_B), backward along C
+    const f2 u0 = fma(c.c6, d2p<B, B>(V, 0, 0, 0), V(B, 0, 0, 0));
+    const f2 u1 = fma(c.c6, d2p<B, B>(V, -cx, -cy, -cz), V(B, -cx, -cy, -cz));
+    return fma(mul(ck<C>(c), fma(u1, m1(), u0)), m1(), r);
+}
+
+template <int RS, int PASSES, bool HJ>
+__global__ void __launch_bounds__(NTH, 2) k3_source2(Geo g, Coef3P c, const float *b0, const float *b1,
+                                                    const float *b2, const float *j0, const float *j1,
+                                                    const float *j2, float *o0, float *o1, float *o2) {
+    using namespace pair2;
+    constexpr int N = HJ ? 6 : 3;
+    constexpr int LA = RS - 3;
+    extern __shared__ __align__(16) unsigned char m3raw[];
+    float *ring = reinterpret_cast<float *>(m3raw);  // [RS][N][PL2]
+    const float *src[6] = {b0, b1, b2, j0, j1, j2};
+    float *out[3] = {o0, o1, o2};
+    const int x0 = blockIdx.x * TX2, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * ZSEG, z1 = min(z0 + ZSEG, g.nz);
+    PairCopies cp;
+    cp.init(g, x0, y0);
+    const int px = x0 + 2 * threadIdx.x, py = y0 + threadIdx.y;
+    const bool inside = px < g.nx && py < g.ny;
+    const int64_t cell = (int64_t)py * g.pitch + px;
+    const int c0 = (threadIdx.y + 1) * RW2 + 2 + 2 * threadIdx.x;
+    auto issue = [&](int m) {
+        if (m == 0) {
+            cp.issue<RS, N>(ring, src, g, z0 - 1);
+            cp.issue<RS, N>(ring, src, g, z0);
+        }
+        if (z0 + 1 + m <= z1) cp.issue<RS, N>(ring, src, g, z0 + 1 + m);
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int m = 0; m < LA; ++m) issue(m);
+    for (int k = z0; k < z1; ++k) {
+        cp_async_wait<LA - 1>();
+        __syncthreads();
+        issue(k - z0 + LA);
+        if (inside) {
+            const int sm1 = ((k - 1) & (RS - 1)) * N * PL2, s0 = (k & (RS - 1)) * N * PL2,
+                      sp1 = ((k + 1) & (RS - 1)) * N * PL2;
+            auto V = [&](int q, int dx, int dy, int dz) -> f2 {
+                const float *row = ring + (dz < 0 ? sm1 : (dz > 0 ? sp1 : s0)) + q * PL2 + c0 + dy * RW2;
+                const f2 pr = *reinterpret_cast<const float2 *>(row);
+                return dx == 0 ? pr : (dx > 0 ? mk(pr.y, row[2]) : mk(row[-1], pr.x));
+            };
+            f2 d[3] = {curl_alpha_b2<0>(V, c), curl_alpha_b2<1>(V, c), curl_alpha_b2<2>(V, c)};
+            if constexpr (HJ) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    f2 jf = mk(0.f, 0.f);
+                    if constexpr (PASSES == 1) {
+                        // separable binomial: weights (1, 2, 1)/4 per axis
+#pragma unroll
+                        for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+                            for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+                                for (int dx = -1; dx <= 1; ++dx) {
+                                    const float w = float((2 - dx * dx) * (2 - dy * dy) * (2 - dz * dz)) * (1.f / 64.f);
+                                    jf = fma(mk(w, w), V(3 + a, dx, dy, dz), jf);
+                                }
+                    } else {
+                        jf = V(3 + a, 0, 0, 0);
+                    }
+                    d[a] = fma(mul(c.q, jf), m1(), d[a]);
+                }
+            }
+            const int64_t idx = (int64_t)k * g.plane + cell;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) *reinterpret_cast<float2 *>(out[q] + idx) = d[q];
+        }
+    }
+    cp_async_wait<0>();
 }
 
 inline dim3 grid3(const Geo &g) { return dim3((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + ZSEG - 1) / ZSEG); }
@@ -196,7 +534,11 @@ bool march3d_supported(int dims, int passes) { return dims == 3 && passes >= 0 &
 
 template <typename T, int N>
 size_t ring_bytes() {
-    return (size_t)4 * N * PL * sizeof(T);
+    return (size_t)RingDepth<T>::RS * N * PL * sizeof(T);
+}
+template <typename T>
+size_t sweep_bytes() {
+    return ring_bytes<T, 3>() + (size_t)RingDepth<T>::RS * 3 * NTH * sizeof(T);
 }
 
 template <typename T, int PASSES, bool HJ>
@@ -212,9 +554,59 @@ void run_source(const Geo &g, const Coef<T> &c, const T *const B[3], const T *co
         g, c, B[0], B[1], B[2], HJ ? J[0] : nullptr, HJ ? J[1] : nullptr, HJ ? J[2] : nullptr, out[0], out[1], out[2]);
 }
 
+bool pair_path(const Geo &g, float *) { return g.nx % 2 == 0 && g.pitch % 2 == 0; }
+
+Coef3P coef3p(const Coef<float> &c) {
+    auto pr = [](float v) { return make_float2(v, v); };
+    return Coef3P{pr(c.ax), pr(c.ay), pr(c.az), pr(c.ayz), pr(c.azx), pr(c.axy), pr(c.byz), pr(c.bzx), pr(c.bxy),
+                  pr(c.c6), pr(c.kx), pr(c.ky), pr(c.kz), pr(c.q)};
+}
+
+constexpr int SRC_RS = 4;  // source ring slots (six components: 65 KB)
+
+template <int PASSES, bool HJ>
+void run_source2(const Geo &g, const Coef<float> &c, const float *const B[3], const float *const J[3],
+                 float *const out[3], cudaStream_t s) {
+    constexpr int N = HJ ? 6 : 3;
+    constexpr size_t bytes = (size_t)SRC_RS * N * PL2 * sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k3_source2<SRC_RS, PASSES, HJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        attr = true;
+    }
+    const dim3 grid((g.nx + TX2 - 1) / TX2, (g.ny + TY - 1) / TY, (g.nz + ZSEG - 1) / ZSEG);
+    k3_source2<SRC_RS, PASSES, HJ><<<grid, dim3(TXP, TY), bytes, s>>>(
+        g, coef3p(c), B[0], B[1], B[2], HJ ? J[0] : nullptr, HJ ? J[1] : nullptr, HJ ? J[2] : nullptr, out[0], out[1],
+        out[2]);
+}
+bool pair_path(const Geo &, double *) { return false; }
+
+template <bool UPD>
+void run_sweep2(const Geo &g, const Coef<float> &c, const float *const dEp[3], const float *const in[3],
+                float *const out[3], cudaStream_t s) {
+    constexpr size_t bytes = (size_t)RingDepth<float>::RS * 3 * PL2 * sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k3_sweep2<UPD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        attr = true;
+    }
+    const Coef3P cp = coef3p(c);
+    const dim3 grid((g.nx + TX2 - 1) / TX2, (g.ny + TY - 1) / TY, (g.nz + ZSEG - 1) / ZSEG);
+    k3_sweep2<UPD><<<grid, dim3(TXP, TY), bytes, s>>>(g, cp, dEp[0], dEp[1], dEp[2], in[0], in[1], in[2], out[0],
+                                                     out[1], out[2]);
+}
+
 template <typename T>
 int launch_march3d_source(const Geo &g, const Coef<T> &c, const T *const B[3], const T *const J[3], int passes,
                           T *const out[3], cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (pair_path(g, (float *)nullptr)) {
+            if (!J || !J[0]) run_source2<0, false>(g, c, B, J, out, s);
+            else if (passes == 1) run_source2<1, true>(g, c, B, J, out, s);
+            else run_source2<0, true>(g, c, B, J, out, s);
+            return 1;
+        }
+    }
     if (!J || !J[0]) run_source<T, 0, false>(g, c, B, J, out, s);
     else if (passes == 1) run_source<T, 1, true>(g, c, B, J, out, s);
     else run_source<T, 0, true>(g, c, B, J, out, s);
@@ -223,13 +615,21 @@ int launch_march3d_source(const Geo &g, const Coef<T> &c, const T *const B[3], c
 
 template <typename T>
 int launch_march3d_sweep(const Geo &g, const Coef<T> &c, const T *const dEp[3], const T *const in[3], T *const out[3],
-                         cudaStream_t s) {
+                         cudaStream_t s, bool update) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (pair_path(g, (float *)nullptr)) {
+            if (update) run_sweep2<true>(g, c, dEp, in, out, s);
+            else run_sweep2<false>(g, c, dEp, in, out, s);
+            return 1;
+        }
+    }
+    if (update) return 0;  // the scalar sweep does not fuse the update: the caller launches it
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k3_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring_bytes<T, 3>());
+        cudaFuncSetAttribute(k3_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_bytes<T>());
         attr = true;
     }
-    k3_sweep<T><<<grid3(g), dim3(TX, TY), ring_bytes<T, 3>(), s>>>(g, c, dEp[0], dEp[1], dEp[2], in[0], in[1], in[2],
+    k3_sweep<T><<<grid3(g), dim3(TX, TY), sweep_bytes<T>(), s>>>(g, c, dEp[0], dEp[1], dEp[2], in[0], in[1], in[2],
                                                                    out[0], out[1], out[2]);
     return 1;
 }
@@ -238,7 +638,7 @@ int launch_march3d_sweep(const Geo &g, const Coef<T> &c, const T *const dEp[3], 
     template int launch_march3d_source<T>(const Geo &, const Coef<T> &, const T *const[3], const T *const[3], int, \
                                           T *const[3], cudaStream_t);                                           \
     template int launch_march3d_sweep<T>(const Geo &, const Coef<T> &, const T *const[3], const T *const[3],       \
-                                         T *const[3], cudaStream_t);
+                                         T *const[3], cudaStream_t, bool);
 FMX_M3_INST(float)
 FMX_M3_INST(double)
 #undef FMX_M3_INST

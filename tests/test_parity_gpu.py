@@ -122,13 +122,17 @@ def test_staged_fp64_3d_1d(fmx, shape):
     assert_parity(Eg, Bg, Eo, Bo, TOL64, f"staged {shape}")
 
 
+@pytest.mark.parametrize("shape", [(37, 11, 70), (70, 11, 37), (8, 6, 5)])
 @pytest.mark.parametrize("kw", [dict(m=4, filter_passes=0), dict(m=2, filter_passes=2), dict(m=1, filter_passes=1),
                                 dict(m=0, filter_passes=1)])
-def test_3d_march_and_staged_branches(fmx, kw):
+def test_3d_march_and_staged_branches(fmx, kw, shape):
     """3D: the z-marching kernels (at most one filter pass on the current;
     several z segments and tiles, ragged in every axis) and the staged
-    fallback (two passes), FP64 and FP32, with and without a current."""
-    shape = (37, 11, 70)
+    fallback (two passes), FP64 and FP32, with and without a current.  Odd
+    n_x takes the one-column FP32 sweep; even n_x the column-pair sweep
+    (with the E update fused into the last sweep), here with a ragged second
+    x tile and an odd number of planes in the last z segment (70, 11, 37),
+    and with n_x below the tile width (8, 6, 5)."""
     E, B, J = _inputs(shape, 33, np.float64)
     for with_j in (True, False):
         Jw = J if with_j else None
