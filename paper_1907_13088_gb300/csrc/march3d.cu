@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(NTH) k3_source(Geo g, Coef<T> c, const T *b0, 
 // by cp.async like the scalar kernel's (8-byte copies of column pairs, 4-byte
 // copies of the two halo columns); dE' of the thread's own pair is prefetched
 // into registers two planes ahead (E^n, when the sweep also applies the update
-// E^{n+1} = E^n + dE, is loaded as the plane's work starts).
+// E^{n+1} = E^n + dE, one plane ahead).
 using pair2::f2;
 constexpr int TXP = 32, TX2 = 2 * TXP;              // threads along x, columns of the tile
 constexpr int RW2 = TX2 + 4, PL2 = RW2 * RH;         // smem row and plane (one component)
@@ -258,6 +258,7 @@ constexpr int NPC = TXP * RH, NCP2 = NPC + 2 * RH;  // pair copies and halo copi
 
 struct Coef3P {
     f2 ax, ay, az, ayz, azx, axy, byz, bzx, bxy, c6, kx, ky, kz, q;
+    f2 q64;  // q / 64: the one-pass 3D binomial with integer weights (exact power-of-two scaling)
 };
 template <int AX>
 __device__ __forceinline__ f2 ck(const Coef3P &c) {
@@ -399,18 +400,18 @@ __global__ void __launch_bounds__(NTH, 2) k3_sweep2(Geo g, Coef3P c, const float
     for (int m = 0; m < LA; ++m) issue(m);
     ldown(z0, 0);
     ldown(z0 + 1, 1);
+    f2 en[3];  // UPD: E^n of the own pair, plane k
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        en[q] = (UPD && inside) ? *reinterpret_cast<const float2 *>(out[q] + (int64_t)z0 * g.plane + cell) : mk(0.f, 0.f);
     auto step = [&](int k, auto bsel) {
         constexpr int b = decltype(bsel)::value;
         cp_async_wait<LA - 1>();
         __syncthreads();
         issue(k - z0 + LA);
-        f2 d[3], e[3];
+        f2 d[3];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            d[q] = pd[b][q];
-            // E^n of the own pair (UPD), loaded before the stencil work that hides it
-            e[q] = (UPD && inside) ? *reinterpret_cast<const float2 *>(out[q] + (int64_t)k * g.plane + cell) : mk(0.f, 0.f);
-        }
+        for (int q = 0; q < 3; ++q) d[q] = pd[b][q];
         ldown(k + 2, b);
         if (inside) {
             const int sm1 = ((k - 1) & (RS - 1)) * 3 * PL2, s0 = (k & (RS - 1)) * 3 * PL2,
@@ -424,9 +425,15 @@ __global__ void __launch_bounds__(NTH, 2) k3_sweep2(Geo g, Coef3P c, const float
             const int64_t idx = (int64_t)k * g.plane + cell;
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                if (UPD) r[q] = add(e[q], r[q]);
+                if (UPD) r[q] = add(en[q], r[q]);
                 *reinterpret_cast<float2 *>(out[q] + idx) = r[q];
             }
+        }
+        // UPD: E^n of the own pair of the next plane, in flight across the barrier
+        if (UPD && inside && k + 1 < z1) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                en[q] = *reinterpret_cast<const float2 *>(out[q] + (int64_t)(k + 1) * g.plane + cell);
         }
     };
     for (int k = z0; k < z1; k += 2) {
@@ -456,7 +463,7 @@ __device__ __forceinline__ f2 curl_alpha_b2(const F &V, const Coef3P &c) {
 }
 
 template <int RS, int PASSES, bool HJ>
-__global__ void __launch_bounds__(NTH, 2) k3_source2(Geo g, Coef3P c, const float *b0, const float *b1,
+__global__ void __launch_bounds__(NTH, 3) k3_source2(Geo g, Coef3P c, const float *b0, const float *b1,
                                                     const float *b2, const float *j0, const float *j1,
                                                     const float *j2, float *o0, float *o1, float *o2) {
     using namespace pair2;
@@ -484,6 +491,29 @@ __global__ void __launch_bounds__(NTH, 2) k3_source2(Geo g, Coef3P c, const floa
     };
 #pragma unroll
     for (int m = 0; m < LA; ++m) issue(m);
+    f2 jz[3][2];  // x-y filtered current of planes k-1, k (own pair)
+    if constexpr (HJ && PASSES == 1) {
+        // planes z0-1 and z0 (copy group 0)
+        cp_async_wait<LA - 1>();
+        __syncthreads();
+        if (inside) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float *pl = ring + ((z0 - 1 + h) & (RS - 1)) * N * PL2 + (3 + a) * PL2 + c0;
+                    f2 acc = mk(0.f, 0.f);
+#pragma unroll
+                    for (int dy = -1; dy <= 1; ++dy) {
+                        const float *row = pl + dy * RW2;
+                        const f2 pr = *reinterpret_cast<const float2 *>(row);
+                        const f2 rowf = fma(pr, cst(2), add(mk(row[-1], pr.x), mk(pr.y, row[2])));
+                        acc = fma(cst(2 - dy * dy), rowf, acc);
+                    }
+                    jz[a][h] = acc;
+                }
+        }
+    }
     for (int k = z0; k < z1; ++k) {
         cp_async_wait<LA - 1>();
         __syncthreads();
@@ -498,24 +528,30 @@ __global__ void __launch_bounds__(NTH, 2) k3_source2(Geo g, Coef3P c, const floa
             };
             f2 d[3] = {curl_alpha_b2<0>(V, c), curl_alpha_b2<1>(V, c), curl_alpha_b2<2>(V, c)};
             if constexpr (HJ) {
+                if constexpr (PASSES == 1) {
+                    // separable binomial, integer weights (1, 2, 1) per axis, 1/64 folded
+                    // into q: the x-y part of plane k+1 from the ring, the z part from the
+                    // x-y results of planes k-1, k, k+1 kept in registers
+                    auto jxy = [&](int a, int dz) {
+                        f2 acc = mk(0.f, 0.f);
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    f2 jf = mk(0.f, 0.f);
-                    if constexpr (PASSES == 1) {
-                        // separable binomial: weights (1, 2, 1)/4 per axis
+                        for (int dy = -1; dy <= 1; ++dy) {
+                            const f2 rowf = fma(V(3 + a, 0, dy, dz), cst(2), add(V(3 + a, -1, dy, dz), V(3 + a, 1, dy, dz)));
+                            acc = fma(cst(2 - dy * dy), rowf, acc);
+                        }
+                        return acc;
+                    };
 #pragma unroll
-                        for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll
-                            for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-                                for (int dx = -1; dx <= 1; ++dx) {
-                                    const float w = float((2 - dx * dx) * (2 - dy * dy) * (2 - dz * dz)) * (1.f / 64.f);
-                                    jf = fma(mk(w, w), V(3 + a, dx, dy, dz), jf);
-                                }
-                    } else {
-                        jf = V(3 + a, 0, 0, 0);
+                    for (int a = 0; a < 3; ++a) {
+                        const f2 jn = jxy(a, 1);
+                        const f2 jsum = fma(jz[a][1], cst(2), add(jz[a][0], jn));
+                        jz[a][0] = jz[a][1];
+                        jz[a][1] = jn;
+                        d[a] = fma(mul(c.q64, jsum), m1(), d[a]);
                     }
-                    d[a] = fma(mul(c.q, jf), m1(), d[a]);
+                } else {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) d[a] = fma(mul(c.q, V(3 + a, 0, 0, 0)), m1(), d[a]);
                 }
             }
             const int64_t idx = (int64_t)k * g.plane + cell;
@@ -559,7 +595,7 @@ bool pair_path(const Geo &g, float *) { return g.nx % 2 == 0 && g.pitch % 2 == 0
 Coef3P coef3p(const Coef<float> &c) {
     auto pr = [](float v) { return make_float2(v, v); };
     return Coef3P{pr(c.ax), pr(c.ay), pr(c.az), pr(c.ayz), pr(c.azx), pr(c.axy), pr(c.byz), pr(c.bzx), pr(c.bxy),
-                  pr(c.c6), pr(c.kx), pr(c.ky), pr(c.kz), pr(c.q)};
+                  pr(c.c6), pr(c.kx), pr(c.ky), pr(c.kz), pr(c.q), pr(c.q * (1.f / 64.f))};
 }
 
 constexpr int SRC_RS = 4;  // source ring slots (six components: 65 KB)
