@@ -279,7 +279,8 @@ def run_ours(args):
 def run_batch(args):
     """256 independent 2D grids (sizes log-uniform in 64..1024 per side,
     Courant fractions uniform in 0.3..0.9, FP32, vacuum, m = 4), advanced by
-    one persistent launch per step replayed from CUDA graphs, with the tile
+    one persistent launch per step and kind of tile (column-pair TE/TM tiles
+    for even n_x, single-column tiles for odd n_x) replayed from CUDA graphs, with the tile
     rows picked by the autotuner; the same grids stepped one fmx_step call per
     grid are timed beside it."""
     import numpy as np
@@ -342,11 +343,13 @@ def run_batch(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batch of 256 independent 2D periodic grids, sizes log-uniform 64..1024 per side "
                                "(seed 1907004), Courant U[0.3, 0.9], FP32, vacuum, m = 4, one persistent launch "
-                               "per step replayed from CUDA graphs, autotuned tile rows",
+                               "per step and kind of tile replayed from CUDA graphs, autotuned tile rows",
                    "cells_total": cells, "grids": len(shapes), "tuned_tile_rows": chosen or "auto",
                    "work_items": bt.items, "single_grid_path_gcells": round(single, 3)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_fused2d_batch<4,0,false,256>",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "kernel": "whole step: k_pol2d_batch<4,0,false,128> (even n_x) + k_fused2d_batch<4,0,false,256> "
+                               "(odd n_x)",
                      "peak_source": peak_src, "bytes_per_cell_step": 48},
         "gpu_launches": int(launches), "clocks": clocks,
     }

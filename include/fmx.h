@@ -288,15 +288,18 @@ fmx_status fmx_gauss_adjoint_run(fmx_grid *g, int64_t n0, int nsteps, void *cons
                                  void *const *jbar, void *work, size_t work_bytes, int reset);
 
 /* ---- Batched step (many independent 2D grids, one launch per step) ----
- * The grids of a batch are advanced together: every step is ONE persistent
+ * The grids of a batch are advanced together: every step is one persistent
  * kernel launch whose CTAs loop over (grid, strip, row-segment) tiles of all
  * grids, longest tiles first; the launches of fmx_batch_step are replayed
  * from CUDA graphs (two steps per graph) captured on first use.  Each grid
  * has its own sizes, cell sizes, dt / Courant number and buffers; all share
  * the precision (FP32), m, the current-filter passes, and the stream, which
  * must not be the legacy default stream (graph capture needs a stream of its
- * own).  Every grid uses the single-column fused tile of the 2D engine, so
- * odd n_x are fine.  The same equations as fmx_step (Secs. 2.2.1-2.2.2). */
+ * own).  Grids with even n_x (unlumped) use the polarisation-split
+ * column-pair tiles of the 2D engine, one CTA per TE or TM half of a tile;
+ * grids with odd n_x or the lumped scheme use its single-column tile, in a
+ * second launch of the same step when the batch has both kinds.  The same
+ * equations as fmx_step (Secs. 2.2.1-2.2.2). */
 typedef struct fmx_batch fmx_batch;
 
 /* Validates each of the n parameter sets (2D, FP32, fixed m, equal m,
@@ -335,7 +338,8 @@ fmx_status fmx_batch_tune(fmx_batch *b, int trial_steps, int *chosen);
  * plain launch).  Asynchronous.  Errors: FMX_ESTATE, FMX_EINVAL, FMX_ECUDA. */
 fmx_status fmx_batch_step(fmx_batch *b, int nsteps);
 
-/* Work items (tiles) of the current work list, and kernels launched. */
+/* Work items (tiles; a column-pair tile counts once for its TE and TM halves)
+ * of the current work list, and kernels launched. */
 int fmx_batch_items(const fmx_batch *b);
 int64_t fmx_batch_launch_count(const fmx_batch *b);
 

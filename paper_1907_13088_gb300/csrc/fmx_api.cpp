@@ -1286,11 +1286,15 @@ struct fmx_batch {
     cudaStream_t stream = nullptr;
     int threads = 0, halo = 0, width = 0, bps = 1, sms = 1;
     size_t smem = 0;
+    // polarisation-split column-pair tiles (even n_x, unlumped), when instantiated
+    bool pol_ok = false;
+    int pwidth = 0, pbps = 1;
+    size_t psmem = 0;
     bool bound = false;
     fmx::BatchGrid *d_grids = nullptr;
-    fmx::BatchItem *d_items = nullptr;
+    fmx::BatchItem *d_items = nullptr;  // pol items, then single-column items
     size_t max_items = 0;
-    int nitems = 0;
+    int nitems = 0, npol = 0;
     int rows_policy = 0;
     int parity = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -1323,30 +1327,42 @@ int batch_rows(const fmx_batch *b, int i) {
     return L < ny ? L : ny;
 }
 
+// grid i runs on the polarisation-split kernels: even n_x, the unlumped
+// scheme (the kernels take 1/6 as a compile-time constant), 32-bit offsets
+bool batch_pol_grid(const fmx_batch *b, int i) {
+    const fmx::BatchGrid &G = b->grids[i];
+    return b->pol_ok && G.g.nx % 2 == 0 && G.c.c6 == 1.f / 6.f && (int64_t)G.g.ny * G.g.pitch < ((int64_t)1 << 31);
+}
+
 fmx_status batch_build(fmx_batch *b) {
-    std::vector<fmx::BatchItem> items;
-    std::vector<double> cost;
+    std::vector<fmx::BatchItem> items[2];  // [0] pol, [1] single column
+    std::vector<double> cost[2];
     const int warm = 3 * b->m + 2 * b->passes + 8;
     for (int i = 0; i < b->n; ++i) {
         fmx::BatchGrid &G = b->grids[i];
+        const int kind = batch_pol_grid(b, i) ? 0 : 1;
         G.L = batch_rows(b, i);
-        G.W = b->width;
+        G.W = kind == 0 ? b->pwidth : b->width;
         G.nstrip = (G.g.nx + G.W - 1) / G.W;
         const int nseg = (G.g.ny + G.L - 1) / G.L;
         for (int st = 0; st < G.nstrip; ++st)
             for (int sg = 0; sg < nseg; ++sg) {
-                items.push_back({i, st, sg});
+                items[kind].push_back({i, st, sg});
                 const int rows = (sg + 1) * G.L <= G.g.ny ? G.L : G.g.ny - sg * G.L;
-                cost.push_back((double)rows + warm);
+                cost[kind].push_back((double)rows + warm);
             }
     }
-    if (items.size() > b->max_items) return fail(FMX_EINVAL, "batch work list larger than its workspace");
-    // longest tiles first
-    std::vector<size_t> order(items.size());
-    for (size_t k = 0; k < order.size(); ++k) order[k] = k;
-    std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
-    std::vector<fmx::BatchItem> sorted(items.size());
-    for (size_t k = 0; k < order.size(); ++k) sorted[k] = items[order[k]];
+    if (items[0].size() + items[1].size() > b->max_items)
+        return fail(FMX_EINVAL, "batch work list larger than its workspace");
+    // each list longest tiles first
+    std::vector<fmx::BatchItem> sorted;
+    for (int kind = 0; kind < 2; ++kind) {
+        std::vector<size_t> order(items[kind].size());
+        for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+        std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[kind][x] > cost[kind][y]; });
+        for (size_t k = 0; k < order.size(); ++k) sorted.push_back(items[kind][order[k]]);
+    }
+    b->npol = (int)items[0].size();
     b->nitems = (int)sorted.size();
     cudaError_t e = cudaMemcpyAsync(b->d_grids, b->grids.data(), sizeof(fmx::BatchGrid) * b->n,
                                     cudaMemcpyHostToDevice, b->stream);
@@ -1359,16 +1375,24 @@ fmx_status batch_build(fmx_batch *b) {
     return FMX_OK;
 }
 
-int batch_blocks(const fmx_batch *b) {
-    const int slots = b->bps * b->sms;
-    return b->nitems < slots ? b->nitems : slots;
-}
-
+// one launch per kind of tile present: the polarisation kernels (each item a
+// TE and a TM half) and the single-column kernel
 fmx_status batch_launch(fmx_batch *b, int parity) {
-    int nl = fmx::launch_fused2d_batch(b->m, b->passes, b->hj, b->d_grids, b->d_items, b->nitems, parity,
-                                       batch_blocks(b), b->smem, b->stream);
-    if (nl < 0) return fail(FMX_EUNSUPPORTED, "batched kernel not instantiated");
-    b->launches += nl;
+    const int nscal = b->nitems - b->npol;
+    if (b->npol > 0) {
+        const int slots = b->pbps * b->sms, want = 2 * b->npol;
+        const int nl = fmx::launch_fused2d_pol_batch(b->m, b->passes, b->hj, b->d_grids, b->d_items, b->npol, parity,
+                                                     want < slots ? want : slots, b->psmem, b->stream);
+        if (nl < 0) return fail(FMX_EUNSUPPORTED, "batched kernel not instantiated");
+        b->launches += nl;
+    }
+    if (nscal > 0) {
+        const int slots = b->bps * b->sms;
+        const int nl = fmx::launch_fused2d_batch(b->m, b->passes, b->hj, b->d_grids, b->d_items + b->npol, nscal,
+                                                 parity, nscal < slots ? nscal : slots, b->smem, b->stream);
+        if (nl < 0) return fail(FMX_EUNSUPPORTED, "batched kernel not instantiated");
+        b->launches += nl;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "batched kernel launch");
     return FMX_OK;
@@ -1446,6 +1470,8 @@ fmx_status fmx_batch_create(const fmx_params *ps, int n, fmx_batch **out) {
         delete b;
         return fail(FMX_EUNSUPPORTED, "no batched kernel for m = %d", ps[0].m);
     }
+    int pt = 0, ph = 0;
+    b->pol_ok = fmx::fused2d_pol_batch_geometry(b->m, 0, false, &pt, &ph, &b->pwidth, &b->psmem, &b->pbps) == 0;
     *out = b;
     return FMX_OK;
 }
@@ -1454,7 +1480,8 @@ size_t fmx_batch_workspace_bytes(const fmx_batch *b) {
     if (!b) return 0;
     // work list bound: the smallest row extent the tuner tries (32 rows)
     size_t items = 0;
-    const int width = b->width > 0 ? b->width : 1;
+    int width = b->width > 0 ? b->width : 1;
+    if (b->pol_ok && b->pwidth > 0 && b->pwidth < width) width = b->pwidth;
     for (int i = 0; i < b->n; ++i) {
         const size_t ns = ((size_t)b->p[i].n[0] + width - 1) / width;
         items += ns * (((size_t)b->p[i].n[1] + 31) / 32 + 1);
@@ -1487,6 +1514,11 @@ fmx_status fmx_batch_bind(fmx_batch *b, const fmx_buffers *bufs, void *work, siz
     if (fmx::fused2d_batch_geometry(b->m, b->hj ? b->passes : 0, b->hj, &b->threads, &b->halo, &b->width, &b->smem,
                                     &b->bps) != 0)
         return fail(FMX_EUNSUPPORTED, "no batched kernel for m = %d, passes = %d", b->m, b->passes);
+    {
+        int pt = 0, ph = 0;
+        b->pol_ok = fmx::fused2d_pol_batch_geometry(b->m, b->hj ? b->passes : 0, b->hj, &pt, &ph, &b->pwidth,
+                                                    &b->psmem, &b->pbps) == 0;
+    }
     int dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) b->sms = 1;
@@ -1563,7 +1595,8 @@ fmx_status fmx_batch_step(fmx_batch *b, int nsteps) {
             cudaError_t e = cudaGraphLaunch(ge, b->stream);
             if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
         }
-        b->launches += left;
+        // kernels per step: one per kind of tile present
+        b->launches += (int64_t)left * ((b->npol > 0) + (b->nitems > b->npol));
     }
     b->steps += nsteps;
     return FMX_OK;

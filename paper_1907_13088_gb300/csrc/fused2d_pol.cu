@@ -73,9 +73,11 @@ struct PolSmem {
     static constexpr int TOTAL = EN + 2 * RP;
 };
 
+// One tile: strip `strip` (W columns written) and segment `seg` (L rows) of a
+// grid, in the shared memory `sm` (PolSmem layout).
 template <int POL, int M, int P, bool HJ, int NT>
-__global__ void __launch_bounds__(NT, 3)
-    k_pol2d(Fused2dArgs<float> a, Geo g, Coef2 c, int W, int L, int nstrip) {
+__device__ __forceinline__ void pol_tile(const Fused2dArgs<float> &a, const Geo &g, const Coef2 &c, int W, int L,
+                                         int strip, int seg, float *sm) {
     using G = PolGeom<M, P, HJ>;
     constexpr int HC = G::HC, PADP = G::PADP, TJ = G::TJ;
     constexpr int RP = NT + 2 * PADP;  // pairs (floats of a half row) per smem row
@@ -84,8 +86,6 @@ __global__ void __launch_bounds__(NT, 3)
     constexpr int NC = S::NC;
     // own values from registers (TE) or read back from smem (TM: 4 blocks/SM leave no room)
     constexpr bool RJ = POL == TE;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    float *sm = reinterpret_cast<float *>(smraw);
     float *s_j = sm + S::J;
     float *s_b = sm + S::B;
     float *s_ay = sm + S::AY;
@@ -96,7 +96,6 @@ __global__ void __launch_bounds__(NT, 3)
     const int tid = threadIdx.x;
     for (int q = tid; q < S::TOTAL; q += NT) sm[q] = 0.f;
 
-    const int strip = blockIdx.x % nstrip, seg = blockIdx.x / nstrip;
     const int x0 = strip * W;
     const int y0 = seg * L;
     const int y1 = min(y0 + L, g.ny);
@@ -467,6 +466,57 @@ __global__ void __launch_bounds__(NT, 3)
     }
 }
 
+template <int POL, int M, int P, bool HJ, int NT>
+__global__ void __launch_bounds__(NT, 3)
+    k_pol2d(Fused2dArgs<float> a, Geo g, Coef2 c, int W, int L, int nstrip) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    pol_tile<POL, M, P, HJ, NT>(a, g, c, W, L, blockIdx.x % nstrip, blockIdx.x / nstrip, reinterpret_cast<float *>(smraw));
+}
+
+// coefficient pairs of the polarisation kernels from the scheme's FP32
+// coefficients; qf = q / 4^(2 passes), exact
+__host__ __device__ inline Coef2 coef2_of(const Coef<float> &c, int passes) {
+    Coef2 k;
+    k.kx = make_float2(c.kx, c.kx);
+    k.ky = make_float2(c.ky, c.ky);
+    const float qf = ldexpf(c.q, -4 * passes);
+    k.qf = make_float2(qf, qf);
+    k.ax = make_float2(c.ax, c.ax);
+    k.ay = make_float2(c.ay, c.ay);
+    k.axy = make_float2(c.axy, c.axy);
+    k.bxy = make_float2(c.bxy, c.bxy);
+    return k;
+}
+
+// Batched step on the polarisation kernels: a persistent loop over 2 x nitems
+// virtual items, item v the TE (v even) or TM (v odd) half of tile items[v/2]
+// of its grid; one launch per step covers both halves of every tile.
+template <int M, int P, bool HJ, int NT>
+__global__ void __launch_bounds__(NT, 3)
+    k_pol2d_batch(const BatchGrid *__restrict__ grids, const BatchItem *__restrict__ items, int nitems, int parity) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float *sm = reinterpret_cast<float *>(smraw);
+    for (int v = blockIdx.x; v < 2 * nitems; v += gridDim.x) {
+        const BatchItem w = items[v >> 1];
+        const BatchGrid &G = grids[w.grid];
+        Fused2dArgs<float> a{};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            a.E[q] = G.E[parity][q];
+            a.B[q] = G.B[parity][q];
+            a.J[q] = HJ ? G.J[q] : nullptr;
+            a.Eo[q] = const_cast<float *>(G.E[1 - parity][q]);
+            a.Bo[q] = const_cast<float *>(G.B[1 - parity][q]);
+        }
+        a.m = M;
+        a.passes = P;
+        const Geo g = G.g;
+        const Coef2 c = coef2_of(G.c, P);
+        if (v & 1) pol_tile<TM, M, P, HJ, NT>(a, g, c, G.W, G.L, w.strip, w.seg, sm);
+        else pol_tile<TE, M, P, HJ, NT>(a, g, c, G.W, G.L, w.strip, w.seg, sm);
+    }
+}
+
 template <int POL, int M, int P, bool HJ>
 struct PolLauncher {
     static constexpr int NT = 128;
@@ -556,18 +606,7 @@ int pol_dispatch(const Geo &g, const Coef2 &c, const Fused2dArgs<float> &a, cuda
     return -1;
 }
 
-Coef2 make_coef2(const Coef<float> &c, int passes) {
-    auto b = [](float v) { return make_float2(v, v); };
-    Coef2 k;
-    k.kx = b(c.kx);
-    k.ky = b(c.ky);
-    k.qf = b(ldexpf(c.q, -4 * passes));  // q / 4^(2p), exact
-    k.ax = b(c.ax);
-    k.ay = b(c.ay);
-    k.axy = b(c.axy);
-    k.bxy = b(c.bxy);
-    return k;
-}
+Coef2 make_coef2(const Coef<float> &c, int passes) { return coef2_of(c, passes); }
 
 }  // namespace
 
@@ -586,6 +625,42 @@ int launch_fused2d_pol(const Geo &g, const Coef<float> &c, const Fused2dArgs<flo
     t_ev = nullptr;
     t_tm = nullptr;
     return n;
+}
+
+int fused2d_pol_batch_geometry(int m, int passes, bool hj, int *threads, int *halo, int *width, size_t *smem,
+                               int *blocks_per_sm) {
+    int rc = -1;
+#define FMX_PBG(MM, PP, HH)                                                                                    \
+    if (m == MM && passes == PP && hj == HH) {                                                               \
+        using Gm = PolGeom<MM, PP, HH>;                                                                     \
+        constexpr int NT = 128;                                                                             \
+        const size_t te = PolLauncher<TE, MM, PP, HH>::smem_bytes(), tm = PolLauncher<TM, MM, PP, HH>::smem_bytes(); \
+        *threads = NT;                                                                                      \
+        *halo = Gm::HC;                                                                                     \
+        *width = 2 * NT - 2 * Gm::HC - 2;                                                                   \
+        *smem = te > tm ? te : tm;                                                                          \
+        auto k = k_pol2d_batch<MM, PP, HH, NT>;                                                             \
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);                   \
+        int nb = 0;                                                                                         \
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NT, *smem) != cudaSuccess || nb < 1) nb = 1; \
+        *blocks_per_sm = nb;                                                                                \
+        rc = 0;                                                                                             \
+    }
+    FMX_PBG(4, 0, false) FMX_PBG(4, 3, true) FMX_PBG(2, 0, false) FMX_PBG(1, 0, false) FMX_PBG(0, 0, false)
+#undef FMX_PBG
+    return rc;
+}
+
+int launch_fused2d_pol_batch(int m, int passes, bool hj, const BatchGrid *grids, const BatchItem *items, int nitems,
+                             int parity, int nblocks, size_t smem, cudaStream_t s) {
+#define FMX_PBL(MM, PP, HH)                                                                       \
+    if (m == MM && passes == PP && hj == HH) {                                                   \
+        k_pol2d_batch<MM, PP, HH, 128><<<nblocks, 128, smem, s>>>(grids, items, nitems, parity); \
+        return 1;                                                                               \
+    }
+    FMX_PBL(4, 0, false) FMX_PBL(4, 3, true) FMX_PBL(2, 0, false) FMX_PBL(1, 0, false) FMX_PBL(0, 0, false)
+#undef FMX_PBL
+    return -1;
 }
 
 Fused2dShape fused2d_pol_shape(const Geo &g, int m, int passes) {
