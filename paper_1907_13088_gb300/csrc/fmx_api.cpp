@@ -456,7 +456,11 @@ fmx_status staged_step(fmx_grid *g) {
             return fail(FMX_ENOCONV, "residual %.3g above tol after %d sweeps", g->last_resid, hs.count);
         }
     }
-    g->launches += fmx::launch_faraday<T>(g->geo, g->p.dims, c, P.E, P.B, g->stream);
+    {
+        const T *e[3] = {P.E[0], P.E[1], P.E[2]};
+        const int n = march ? fmx::launch_march3d_faraday<T>(g->geo, c, e, P.B, g->stream) : 0;
+        g->launches += n ? n : fmx::launch_faraday<T>(g->geo, g->p.dims, c, P.E, P.B, g->stream);
+    }
     s = check_launch(g, "staged step launch");
     if (s != FMX_OK) return s;
     if (g->p.filter_target == FMX_FILTER_FIELDS && g->p.filter_passes > 0) {

@@ -107,6 +107,10 @@ int launch_march3d_source(const Geo &g, const Coef<T> &c, const T *const B[3], c
 template <typename T>
 int launch_march3d_sweep(const Geo &g, const Coef<T> &c, const T *const dEp[3], const T *const in[3], T *const out[3],
                          cudaStream_t s, bool update = false);
+// Faraday of the 3D FP32 column-pair path; returns 0 (nothing launched) where
+// that path does not apply
+template <typename T>
+int launch_march3d_faraday(const Geo &g, const Coef<T> &c, const T *const E[3], T *const B[3], cudaStream_t s);
 
 // Diagnostics (diag.cu): writes 6 FP64 values to out_dev (w_scheme sum,
 // w_plain sum, divb max, divb sum sq, gauss max, gauss sum sq).

@@ -562,6 +562,80 @@ __global__ void __launch_bounds__(NTH, 3) k3_source2(Geo g, Coef3P c, const floa
     cp_async_wait<0>();
 }
 
+// B -= c dt curl E^{n+1} (Eqs. faraday_x..z) on a column pair, 3D: forward
+// differences (curl_e in stencil.cuh) of E from the plane ring
+template <int A, typename F>
+__device__ __forceinline__ f2 curl_e2(const F &V, const Coef3P &c) {
+    using namespace pair2;
+    constexpr int B = (A + 1) % 3, C = (A + 2) % 3;
+    constexpr int bx = B == 0, by = B == 1, bz = B == 2, cx = C == 0, cy = C == 1, cz = C == 2;
+    const f2 r = mul(ck<B>(c), fma(V(C, 0, 0, 0), m1(), V(C, bx, by, bz)));
+    return fma(mul(ck<C>(c), fma(V(B, 0, 0, 0), m1(), V(B, cx, cy, cz))), m1(), r);
+}
+
+__global__ void __launch_bounds__(NTH, 3) k3_faraday2(Geo g, Coef3P c, const float *e0, const float *e1,
+                                                     const float *e2, float *b0, float *b1, float *b2) {
+    using namespace pair2;
+    constexpr int RS = RingDepth<float>::RS, LA = RingDepth<float>::LA;
+    extern __shared__ __align__(16) unsigned char m3raw[];
+    float *ring = reinterpret_cast<float *>(m3raw);  // [RS][3][PL2] E^{n+1} planes
+    const float *in[3] = {e0, e1, e2};
+    float *bo[3] = {b0, b1, b2};
+    const int x0 = blockIdx.x * TX2, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * ZSEG, z1 = min(z0 + ZSEG, g.nz);
+    PairCopies cp;
+    cp.init(g, x0, y0);
+    const int px = x0 + 2 * threadIdx.x, py = y0 + threadIdx.y;
+    const bool inside = px < g.nx && py < g.ny;
+    const int64_t cell = (int64_t)py * g.pitch + px;
+    const int c0 = (threadIdx.y + 1) * RW2 + 2 + 2 * threadIdx.x;
+    auto issue = [&](int m) {
+        if (m == 0) cp.issue<RS>(ring, in, g, z0);
+        if (z0 + 1 + m <= z1) cp.issue<RS>(ring, in, g, z0 + 1 + m);
+        cp_async_commit();
+    };
+    // B of the own pair, planes k and k+1: two register buffers
+    f2 pb[2][3];
+    auto ldown = [&](int k, int b) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            pb[b][q] = mk(0.f, 0.f);
+            if (inside && k < z1) pb[b][q] = *reinterpret_cast<const float2 *>(bo[q] + (int64_t)k * g.plane + cell);
+        }
+    };
+#pragma unroll
+    for (int m = 0; m < LA; ++m) issue(m);
+    ldown(z0, 0);
+    ldown(z0 + 1, 1);
+    auto step = [&](int k, auto bsel) {
+        constexpr int b = decltype(bsel)::value;
+        cp_async_wait<LA - 1>();
+        __syncthreads();
+        issue(k - z0 + LA);
+        f2 bv[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) bv[q] = pb[b][q];
+        ldown(k + 2, b);
+        if (inside) {
+            const int s0 = (k & (RS - 1)) * 3 * PL2, sp1 = ((k + 1) & (RS - 1)) * 3 * PL2;
+            auto V = [&](int q, int dx, int dy, int dz) -> f2 {
+                const float *row = ring + (dz > 0 ? sp1 : s0) + q * PL2 + c0 + dy * RW2;
+                const f2 pr = *reinterpret_cast<const float2 *>(row);
+                return dx == 0 ? pr : (dx > 0 ? mk(pr.y, row[2]) : mk(row[-1], pr.x));
+            };
+            const f2 r[3] = {curl_e2<0>(V, c), curl_e2<1>(V, c), curl_e2<2>(V, c)};
+            const int64_t idx = (int64_t)k * g.plane + cell;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) *reinterpret_cast<float2 *>(bo[q] + idx) = fma(r[q], m1(), bv[q]);
+        }
+    };
+    for (int k = z0; k < z1; k += 2) {
+        step(k, std::integral_constant<int, 0>());
+        if (k + 1 < z1) step(k + 1, std::integral_constant<int, 1>());
+    }
+    cp_async_wait<0>();
+}
+
 inline dim3 grid3(const Geo &g) { return dim3((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + ZSEG - 1) / ZSEG); }
 
 }  // namespace
@@ -650,6 +724,24 @@ int launch_march3d_source(const Geo &g, const Coef<T> &c, const T *const B[3], c
 }
 
 template <typename T>
+int launch_march3d_faraday(const Geo &g, const Coef<T> &c, const T *const E[3], T *const B[3], cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (pair_path(g, (float *)nullptr)) {
+            constexpr size_t bytes = (size_t)RingDepth<float>::RS * 3 * PL2 * sizeof(float);
+            static bool attr = false;
+            if (!attr) {
+                cudaFuncSetAttribute(k3_faraday2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+                attr = true;
+            }
+            const dim3 grid((g.nx + TX2 - 1) / TX2, (g.ny + TY - 1) / TY, (g.nz + ZSEG - 1) / ZSEG);
+            k3_faraday2<<<grid, dim3(TXP, TY), bytes, s>>>(g, coef3p(c), E[0], E[1], E[2], B[0], B[1], B[2]);
+            return 1;
+        }
+    }
+    return 0;  // FP64 or odd n_x: the caller launches the one-thread-per-cell kernel
+}
+
+template <typename T>
 int launch_march3d_sweep(const Geo &g, const Coef<T> &c, const T *const dEp[3], const T *const in[3], T *const out[3],
                          cudaStream_t s, bool update) {
     if constexpr (std::is_same<T, float>::value) {
@@ -674,7 +766,8 @@ int launch_march3d_sweep(const Geo &g, const Coef<T> &c, const T *const dEp[3], 
     template int launch_march3d_source<T>(const Geo &, const Coef<T> &, const T *const[3], const T *const[3], int, \
                                           T *const[3], cudaStream_t);                                           \
     template int launch_march3d_sweep<T>(const Geo &, const Coef<T> &, const T *const[3], const T *const[3],       \
-                                         T *const[3], cudaStream_t, bool);
+                                         T *const[3], cudaStream_t, bool);                                        \
+    template int launch_march3d_faraday<T>(const Geo &, const Coef<T> &, const T *const[3], T *const[3], cudaStream_t);
 FMX_M3_INST(float)
 FMX_M3_INST(double)
 #undef FMX_M3_INST
