@@ -279,8 +279,8 @@ def run_ours(args):
 def run_batch(args):
     """256 independent 2D grids (sizes log-uniform in 64..1024 per side,
     Courant fractions uniform in 0.3..0.9, FP32, vacuum, m = 4), advanced by
-    one persistent launch per step and kind of tile (column-pair TE/TM tiles
-    for even n_x, single-column tiles for odd n_x) replayed from CUDA graphs, with the tile
+    one persistent launch per step (column-pair TE/TM tiles) replayed from
+    CUDA graphs, with the tile
     rows picked by the autotuner; the same grids stepped one fmx_step call per
     grid are timed beside it."""
     import numpy as np
@@ -343,13 +343,12 @@ def run_batch(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batch of 256 independent 2D periodic grids, sizes log-uniform 64..1024 per side "
                                "(seed 1907004), Courant U[0.3, 0.9], FP32, vacuum, m = 4, one persistent launch "
-                               "per step and kind of tile replayed from CUDA graphs, autotuned tile rows",
+                               "per step replayed from CUDA graphs, autotuned tile rows",
                    "cells_total": cells, "grids": len(shapes), "tuned_tile_rows": chosen or "auto",
                    "work_items": bt.items, "single_grid_path_gcells": round(single, 3)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
-                     "kernel": "whole step: k_pol2d_batch<4,0,false,128> (even n_x) + k_fused2d_batch<4,0,false,256> "
-                               "(odd n_x)",
+                     "kernel": "k_pol2d_batch<4,0,false,128> (whole step)",
                      "peak_source": peak_src, "bytes_per_cell_step": 48},
         "gpu_launches": int(launches), "clocks": clocks,
     }
@@ -412,13 +411,14 @@ def run_adjoint(args):
 def run_3d(args):
     """3D periodic 512^3 FP32, six components, power-law spectrum up to
     k_max = N/8, solenoidal current (width 16), m = 4, one binomial pass on
-    the current every step, dt = 0.5 dt_CFL."""
+    the current every step, dt = 0.5 dt_CFL.  --n3d picks another cube side
+    (for profiler captures on a smaller case; the benchmark line is 512)."""
     import numpy as np
     import torch
     from paper_1907_13088_gb300 import build, synth
     build.build()
     from paper_1907_13088_gb300 import fmx
-    n = 512
+    n = args.n3d
     t0 = time.perf_counter()
     E, B = synth.power_law_fields((n, n, n), n // 8, 1907003, dtype=np.float32)
     J = synth.solenoidal_current((n, n, n), 1907013, width=16.0, rms=1e-3, dtype=np.float32)
@@ -451,7 +451,7 @@ def run_3d(args):
         "metric": METRIC, "value": round(cells * args.steps / (ms / 1e3) / 1e9, 3), "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "3D periodic 512^3 FP32, power-law spectrum k_max=N/8, solenoidal J (width 16), "
+        "config": {"workload": f"3D periodic {n}^3 FP32, power-law spectrum k_max=N/8, solenoidal J (width 16), "
                                "m=4, 1 binomial pass on J each step, dt=0.5 dt_CFL",
                    "engine": "staged" if g.launches - l0 > args.steps else "fused", "input_generation_s": round(gen_s, 1)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -535,6 +535,7 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--workload", choices=("2d4096", "batch256", "adjoint1024", "3d512"), default="2d4096")
+    ap.add_argument("--n3d", type=int, default=512, help="cube side of the 3d512 workload (profiler captures only)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -295,11 +295,10 @@ fmx_status fmx_gauss_adjoint_run(fmx_grid *g, int64_t n0, int nsteps, void *cons
  * has its own sizes, cell sizes, dt / Courant number and buffers; all share
  * the precision (FP32), m, the current-filter passes, and the stream, which
  * must not be the legacy default stream (graph capture needs a stream of its
- * own).  Grids with even n_x (unlumped) use the polarisation-split
- * column-pair tiles of the 2D engine, one CTA per TE or TM half of a tile;
- * grids with odd n_x or the lumped scheme use its single-column tile, in a
- * second launch of the same step when the batch has both kinds.  The same
- * equations as fmx_step (Secs. 2.2.1-2.2.2). */
+ * own).  Grids of the unlumped scheme use the polarisation-split column-pair
+ * tiles of the 2D engine, one CTA per TE or TM half of a tile; lumped grids
+ * use its single-column tile, in a second launch of the same step when the
+ * batch has both kinds.  The same equations as fmx_step (Secs. 2.2.1-2.2.2). */
 typedef struct fmx_batch fmx_batch;
 
 /* Validates each of the n parameter sets (2D, FP32, fixed m, equal m,

@@ -1331,11 +1331,11 @@ int batch_rows(const fmx_batch *b, int i) {
     return L < ny ? L : ny;
 }
 
-// grid i runs on the polarisation-split kernels: even n_x, the unlumped
-// scheme (the kernels take 1/6 as a compile-time constant), 32-bit offsets
+// grid i runs on the polarisation-split kernels: the unlumped scheme (the
+// kernels take 1/6 as a compile-time constant), 32-bit offsets
 bool batch_pol_grid(const fmx_batch *b, int i) {
     const fmx::BatchGrid &G = b->grids[i];
-    return b->pol_ok && G.g.nx % 2 == 0 && G.c.c6 == 1.f / 6.f && (int64_t)G.g.ny * G.g.pitch < ((int64_t)1 << 31);
+    return b->pol_ok && G.c.c6 == 1.f / 6.f && (int64_t)G.g.ny * G.g.pitch < ((int64_t)1 << 31);
 }
 
 fmx_status batch_build(fmx_batch *b) {

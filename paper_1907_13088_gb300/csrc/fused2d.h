@@ -88,8 +88,8 @@ int fused2d_batch_geometry(int m, int passes, bool hj, int *threads, int *halo, 
 int launch_fused2d_batch(int m, int passes, bool hj, const BatchGrid *grids, const BatchItem *items, int nitems,
                          int parity, int nblocks, size_t smem, cudaStream_t s);
 // The same on the polarisation-split column-pair kernels (fused2d_pol.cu) for
-// grids with even n_x and the unlumped scheme: one launch runs the TE and the
-// TM half of every item.
+// grids of the unlumped scheme: one launch runs the TE and the TM half of
+// every item.
 int fused2d_pol_batch_geometry(int m, int passes, bool hj, int *threads, int *halo, int *width, size_t *smem,
                                int *blocks_per_sm);
 int launch_fused2d_pol_batch(int m, int passes, bool hj, const BatchGrid *grids, const BatchItem *items, int nitems,

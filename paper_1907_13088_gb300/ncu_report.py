@@ -22,7 +22,7 @@ import os
 import sys
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-KERNEL_SOURCES = ("fused2d_pol.cu", "fused2d.h", "fmx_internal.h")
+KERNEL_SOURCES = ("fused2d_pol.cu", "pol_tile.cuh", "pair2.cuh", "fused2d.h", "fmx_internal.h")
 
 
 def kernel_hash() -> str:

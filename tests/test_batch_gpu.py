@@ -1,8 +1,8 @@
 """Batched step (many independent 2D grids, one persistent launch per step
 and kind of tile, graph-replayed) against the FP64 oracle per grid and
 against the single-grid path; the tile row extent picked by the autotuner
-must not change any result.  Grids with even n_x run on the column-pair TE/TM
-tiles, grids with odd n_x on the single-column tile."""
+must not change any result.  The grids (odd and even n_x) run on the
+column-pair TE/TM tiles."""
 import numpy as np
 import pytest
 
@@ -52,15 +52,16 @@ def test_batch_matches_oracle_and_single_grid(fmx, nsteps):
         g.step(nsteps)
         Es, Bs, _ = g.get_fields()
         assert rel_l2(Eg, Es) < TOL32 and rel_l2(Bg, Bs) < TOL32
-    assert b.launches == 2 * nsteps  # SHAPES mix even and odd n_x: both kinds of tile every step
+    assert b.launches == nsteps
 
 
 @pytest.mark.parametrize("m", [0, 1, 2, 4])
 def test_batch_column_pair_tiles_every_m(fmx, m):
-    """Even n_x only: one launch per step on the column-pair tiles, every
-    instantiated m, grids from 2 to 1024 columns (one tile narrower than a
-    strip, several strips, rows below the warm-up depth)."""
-    shapes = [(64, 64), (300, 71), (128, 257), (1024, 40), (96, 33), (2, 5), (258, 3), (512, 512)]
+    """One launch per step on the column-pair tiles, every instantiated m,
+    grids from 1 to 1024 columns, odd and even (one tile narrower than a
+    strip, several strips, seam strips of odd n_x, rows below the warm-up
+    depth)."""
+    shapes = [(64, 64), (300, 71), (128, 257), (1024, 40), (97, 33), (1, 5), (259, 3), (511, 512)]
     cfs = [0.3, 0.5, 0.75, 0.61, 0.33, 0.9, 0.45, 0.8]
     b = fmx.Batch(shapes, cfs, m=m)
     inputs = [_fields(sh, 1907140 + i) for i, sh in enumerate(shapes)]

@@ -90,10 +90,11 @@ def test_fused_fp64_every_instantiation(fmx, m, passes):
 @pytest.mark.parametrize("m", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("passes", [0, 1, 2, 3, None])
 def test_fused_fp32_every_instantiation(fmx, m, passes):
-    """FP32 fused path: the polarisation-split kernels (even n_x; 556 has
-    three strips, the first and last wrapping the periodic seam) and the
-    single-kernel path (odd n_x), every (m, passes) pair, several strips and
-    segments, against the oracle with FP32-rounded coefficients."""
+    """FP32 fused path, the polarisation-split kernels: even n_x (556 has
+    three strips, the first and last wrapping the periodic seam) and odd n_x
+    (261: seam strips with single-column loads), every (m, passes) pair,
+    several strips and segments, against the oracle with FP32-rounded
+    coefficients."""
     for shape in ((262, 97), (556, 97), (261, 97)):
         E, B, J = _inputs(shape, 200 + m, np.float32, with_j=passes is not None, smooth=True)
         p = passes or 0
@@ -104,8 +105,12 @@ def test_fused_fp32_every_instantiation(fmx, m, passes):
         assert_parity(Eg, Bg, Eo, Bo, TOL32, f"fused fp32 {shape} m={m} p={passes}")
 
 
-@pytest.mark.parametrize("shape", [(2, 2), (4, 3), (2, 9), (600, 2), (1030, 6), (272, 3), (276, 1)])
+@pytest.mark.parametrize("shape", [(2, 2), (4, 3), (2, 9), (600, 2), (1030, 6), (272, 3), (276, 1),
+                                   (1, 8), (3, 5), (5, 3), (7, 1), (257, 9), (511, 33), (513, 40)])
 def test_fused_fp32_small_and_thin(fmx, shape):
+    """Small, thin and odd-n_x FP32 grids on the fused path: with odd n_x the
+    strips that cross the periodic seam load single columns (n_x = 1 to 513:
+    one strip, two, three with an interior strip)."""
     E, B, J = _inputs(shape, 301, np.float32)
     Eg, Bg, _ = _run_gpu(fmx, shape, E, B, J, 5, precision=0, m=4, filter_passes=3, engine=2)
     Eo, Bo, rc, _ = _oracle(shape, E.astype(np.float64), B.astype(np.float64), J.astype(np.float64), 5, m=4,
