@@ -50,6 +50,23 @@ def _dist():
     return rank, world, local
 
 
+def max_over_ranks(x, world, device):
+    """The largest of every rank's x (a time): an all-reduce MAX when world > 1
+    (NCCL on the GPU runs, gloo in the CPU tests)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(cells_per_rank, steps, seconds_max, world):
+    """Gcell-updates/s of the whole job: the cell updates of all ranks over the
+    slowest rank's time (replicas: every rank advances its own grid)."""
+    return world * cells_per_rank * steps / seconds_max / 1e9
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -196,10 +213,7 @@ def run_ours(args):
     barrier()
     launches = g.launches - l0
     ms = ev0.elapsed_time(ev1)
-    t_rank = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_rank, op=dist.ReduceOp.MAX)
-    ms_max = float(t_rank.item())
+    ms_max = max_over_ranks(ms, world, "cuda")
     clocks = sampler.summary(t0, t1) if rank == 0 else None
     sampler.stop()
 
@@ -224,10 +238,7 @@ def run_ours(args):
         g.get_fields(fmx.FMX_E | fmx.FMX_B, host_out=hout)
     torch.cuda.synchronize()
     te1 = time.perf_counter()
-    e2e_s = torch.tensor([te1 - te0], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
-    e2e_value = world * cells * e2e_steps / float(e2e_s.item()) / 1e9
+    e2e_value = whole_job_rate(cells, e2e_steps, max_over_ranks(te1 - te0, world, "cuda"), world)
 
     # per-kernel durations, CUDA events on the launching stream, after the timed region
     prof_steps = max(50, min(500, args.steps))
@@ -239,7 +250,7 @@ def run_ours(args):
     cpu = cpu_baseline(E, B, J) if (rank == 0 and args.cpu_baseline) else None
 
     if rank == 0:
-        value = world * cells * args.steps / (ms_max / 1e3) / 1e9
+        value = whole_job_rate(cells, args.steps, ms_max / 1e3, world)
         peak, peak_src = _peaks()
         dom = max(kstats, key=lambda k: k["total_ms"])
         per_launch_s = dom["total_ms"] / 1e3 / dom["launches"]
