@@ -178,6 +178,19 @@ fmx_status fmx_set_fields(fmx_grid *g, unsigned mask, const void *const *src, in
  * were bound as NULL. */
 fmx_status fmx_set_current(fmx_grid *g, const void *const *src, int where);
 
+/* Time profile of the current, the callback-free form of a current with a
+ * fixed spatial shape and a prescribed time dependence (the current enters
+ * the step at t = (n + 1/2) dt, Sec. 2): for the next len steps that fmx_step
+ * advances, step k of them (k = 0 .. len-1) uses j^{n+1/2} = table[k] * J,
+ * J the bound current; after the table runs out, J as it is.  The factor
+ * scales the current's coefficient 4 pi dt of that step (computed in FP64,
+ * then rounded to the storage precision).  The table (host memory, len
+ * doubles) is copied; len = 0 clears it.  It applies to the forward step
+ * (also inside fmx_gauss_run), not to fmx_adjoint_step or the batch.
+ * Errors: FMX_EINVAL (len < 0, table NULL with len > 0, a non-finite
+ * entry), FMX_ESTATE (not bound, or J buffers bound as NULL). */
+fmx_status fmx_set_current_profile(fmx_grid *g, const double *table, int len);
+
 /* Enqueues nsteps full steps (1..6 above) on the stream.  Fixed mode never
  * synchronises.  Residual mode reads the device residual back every few
  * sweeps (synchronising) and returns FMX_ENOCONV if a solve reaches m_max.

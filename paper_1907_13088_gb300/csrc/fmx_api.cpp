@@ -4,6 +4,8 @@
 // every device buffer is borrowed from the caller.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <cmath>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -236,6 +238,8 @@ struct fmx_grid {
     fmx_params p;
     double dt = 0.0;
     double co[FMX_NCOEF];
+    std::vector<double> jprof;  // time profile of the current (fmx_set_current_profile)
+    size_t jprof_pos = 0;
     int engine = FMX_ENGINE_STAGED;
     fmx::Geo geo;
     size_t elem = 4;
@@ -371,9 +375,18 @@ fmx_status filtered_current(fmx_grid *g, const T *jsrc[3]) {
     return check_launch(g, "current filter launch");
 }
 
+// coefficients of the next step: the current's 4 pi dt times the next entry of
+// the time profile while one is left (consumed here)
+template <typename T>
+fmx::Coef<T> step_coef(fmx_grid *g) {
+    fmx::Coef<T> c = make_coef<T>(g->co);
+    if (g->jprof_pos < g->jprof.size()) c.q = (T)(g->co[3] * g->jprof[g->jprof_pos++]);
+    return c;
+}
+
 template <typename T>
 fmx_status staged_step(fmx_grid *g) {
-    const fmx::Coef<T> c = make_coef<T>(g->co);
+    const fmx::Coef<T> c = step_coef<T>(g);
     fmx::StagedPtrs<T> P = staged_ptrs<T>(g);
     const int mode = g->p.iter_mode;
     const bool cheb = mode == FMX_ITER_CHEB_FIXED || mode == FMX_ITER_CHEB_RESIDUAL;
@@ -486,13 +499,13 @@ cudaEvent_t *profile_events(fmx_grid *g, size_t n) {
 
 template <typename T>
 fmx_status fused_step(fmx_grid *g, int nsteps) {
-    const fmx::Coef<T> c = make_coef<T>(g->co);
+    const fmx::Coef<T> c0 = make_coef<T>(g->co);
     // TE/TM kernels: the TE and TM chains touch disjoint components, so the TM
     // launches go to a second stream, forked from and joined back into the
     // grid's stream (not when profiling: the events time one stream)
     bool two = false;
     if constexpr (sizeof(T) == 4)
-        two = nsteps > 0 && !g->prof && fmx::fused2d_pol_supported(g->geo) && c.c6 == 1.f / 6.f;
+        two = nsteps > 0 && !g->prof && fmx::fused2d_pol_supported(g->geo) && c0.c6 == 1.f / 6.f;
     if (two) {
         cudaError_t e = cudaSuccess;
         if (!g->s_tm) e = cudaStreamCreateWithFlags(&g->s_tm, cudaStreamNonBlocking);
@@ -503,6 +516,7 @@ fmx_status fused_step(fmx_grid *g, int nsteps) {
         if (e != cudaSuccess) return cuda_fail(e, "TM stream fork");
     }
     for (int n = 0; n < nsteps; ++n) {
+        const fmx::Coef<T> c = step_coef<T>(g);
         const int nxt = 1 - g->cur;
         fmx::Fused2dArgs<T> a{};
         for (int q = 0; q < 3; ++q) {
@@ -792,6 +806,18 @@ fmx_status fmx_set_fields(fmx_grid *g, unsigned mask, const void *const *src, in
         cudaError_t e = cudaStreamSynchronize(g->stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     }
+    return FMX_OK;
+}
+
+fmx_status fmx_set_current_profile(fmx_grid *g, const double *table, int len) {
+    if (!g) return fail(FMX_EINVAL, "NULL grid");
+    if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
+    if (!g->buf.J[0]) return fail(FMX_ESTATE, "no J buffers bound");
+    if (len < 0 || (len > 0 && !table)) return fail(FMX_EINVAL, "bad table");
+    for (int k = 0; k < len; ++k)
+        if (!std::isfinite(table[k])) return fail(FMX_EINVAL, "table[%d] is not finite", k);
+    g->jprof.assign(table, table + len);
+    g->jprof_pos = 0;
     return FMX_OK;
 }
 

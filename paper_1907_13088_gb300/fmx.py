@@ -78,6 +78,7 @@ def _load():
         "fmx_bind": (ctypes.c_int, [G, ctypes.POINTER(fmx_buffers)]),
         "fmx_set_fields": (ctypes.c_int, [G, ctypes.c_uint, vpp, ctypes.c_int]),
         "fmx_set_current": (ctypes.c_int, [G, vpp, ctypes.c_int]),
+        "fmx_set_current_profile": (ctypes.c_int, [G, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
         "fmx_step": (ctypes.c_int, [G, ctypes.c_int]),
         "fmx_filter": (ctypes.c_int, [G, ctypes.c_uint, ctypes.c_int]),
         "fmx_get_fields": (ctypes.c_int, [G, ctypes.c_uint, vpp, ctypes.c_int]),
@@ -139,6 +140,7 @@ fmx_workspace_bytes = _lib.fmx_workspace_bytes
 fmx_bind = _lib.fmx_bind
 fmx_set_fields = _lib.fmx_set_fields
 fmx_set_current = _lib.fmx_set_current
+fmx_set_current_profile = _lib.fmx_set_current_profile
 fmx_step = _lib.fmx_step
 fmx_filter = _lib.fmx_filter
 fmx_get_fields = _lib.fmx_get_fields
@@ -311,6 +313,12 @@ class Grid:
         where = FMX_HOST if isinstance(J, np.ndarray) else FMX_DEVICE
         check(fmx_set_current(self.handle, ptrs, where), "fmx_set_current")
         del keep
+
+    def set_current_profile(self, table):
+        """j^{n+1/2} = table[k] * J for the next len(table) steps (fmx_set_current_profile)."""
+        t = np.ascontiguousarray(table, dtype=np.float64)
+        check(fmx_set_current_profile(self.handle, t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(t.size)),
+              "fmx_set_current_profile")
 
     def get_fields(self, mask=FMX_E | FMX_B, out=None, host_out=None):
         """Copies the components in mask to host numpy arrays (``host_out``

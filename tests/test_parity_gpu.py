@@ -369,3 +369,34 @@ def test_conservation_on_gpu_fp64(fmx):
     db = core.div_b(p, Bg) - core.div_b(p, B)
     assert np.max(np.abs(db)) < 1e-11
     assert abs(d1["divb_l2"] - d0["divb_l2"]) < 1e-10 * d0["divb_l2"]
+
+
+@pytest.mark.parametrize("case", [
+    dict(shape=(37, 29), precision=1, engine=2, kw=dict(m=4, filter_passes=3)),
+    dict(shape=(262, 97), precision=0, engine=2, kw=dict(m=4, filter_passes=3)),
+    dict(shape=(70, 11, 37), precision=0, engine=1, kw=dict(m=4, filter_passes=1, courant=0.6)),
+    dict(shape=(13, 11, 7), precision=1, engine=1, kw=dict(m=3, filter_passes=2, courant=0.7)),
+], ids=["fused-fp64", "pol-fp32", "march3d-fp32", "staged-fp64"])
+def test_current_time_profile(fmx, case):
+    """fmx_set_current_profile: step k uses table[k] * J for the length of the
+    table, J itself afterwards; against the oracle stepped one step at a time
+    with the scaled current."""
+    shape, prec = case["shape"], case["precision"]
+    dt_ = np.float64 if prec == 1 else np.float32
+    E, B, J = _inputs(shape, 71, dt_, smooth=prec == 0)
+    table = [0.5, -1.25, 2.0, 0.0]
+    nsteps = 6
+    g = fmx.Grid(shape, precision=prec, engine=case["engine"], **case["kw"])
+    g.set_fields(E, B)
+    g.set_current(J)
+    g.set_current_profile(table)
+    g.step(nsteps)
+    Eg, Bg, _ = g.get_fields()
+    g.close()
+    p = core.Params(shape=tuple(shape), coef_f32=prec == 0, **case["kw"])
+    Eo, Bo = E.astype(np.float64), B.astype(np.float64)
+    for k in range(nsteps):
+        f = table[k] if k < len(table) else 1.0
+        Eo, Bo, _, _ = core.step(p, Eo, Bo, f * J.astype(np.float64), 1)
+    assert_parity(np.array(Eg, dtype=np.float64), np.array(Bg, dtype=np.float64), Eo, Bo,
+                  TOL64 if prec == 1 else TOL32, f"current profile {case}")
