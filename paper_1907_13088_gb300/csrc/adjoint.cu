@@ -112,49 +112,79 @@ struct GaussArgs {
     int np;
 };
 
-// shared layout: gx[np][GTX], gy[np][GTY] (gy pre-scaled by a_p in the source);
-// amp: np doubles of shared memory for the amplitudes (source only)
+// shared layout: par[3][np] (source centre x, y and, in the synthesis, the
+// amplitude, in T), gx[np][GTX], gy[np][GTY] (gy pre-scaled by a_p in the
+// source).  The per-source values are converted from FP64 once per block
+// (FP64 work is slow on this part: doing it per profile element cost more
+// than the rest of the kernel).
+template <typename T>
+__device__ __forceinline__ void gauss_params(const GaussArgs &a, bool scale, T *par) {
+    for (int p = threadIdx.x; p < a.np; p += blockDim.x) {
+        par[p] = (T)a.cxy[2 * p];
+        par[a.np + p] = (T)a.cxy[2 * p + 1];
+        if (scale) par[2 * a.np + p] = (T)(a.amp ? a.amp[p] : a.theta[p] * sin(a.omega0 * a.t + a.phi[p]));
+    }
+}
+
+// the tile's 1D profiles from par (gauss_params, synchronised before)
 template <typename T>
 __device__ __forceinline__ void gauss_profiles(const Geo &g, const GaussArgs &a, int x0, int y0, bool scale, T *gx,
-                                               T *gy, double *amp) {
+                                               T *gy, const T *par) {
     const T nx = (T)g.nx, ny = (T)g.ny, k = (T)a.inv2w2;
-    if (scale) {  // one amplitude per source (an FP64 sin each), then the profiles
-        for (int p = threadIdx.x; p < a.np; p += blockDim.x)
-            amp[p] = a.amp ? a.amp[p] : a.theta[p] * sin(a.omega0 * a.t + a.phi[p]);
-        __syncthreads();
-    }
     for (int q = threadIdx.x; q < a.np * GTX; q += blockDim.x) {
         const int p = q / GTX, i = x0 + q % GTX;
-        const T dx = pdist<T>((T)i - (T)a.cxy[2 * p], nx);
+        const T dx = pdist<T>((T)i - par[p], nx);
         gx[q] = gexp<T>(-dx * dx * k);
     }
     for (int q = threadIdx.x; q < a.np * GTY; q += blockDim.x) {
         const int p = q / GTY, j = y0 + q % GTY;
-        const T dy = pdist<T>((T)j - (T)a.cxy[2 * p + 1], ny);
+        const T dy = pdist<T>((T)j - par[a.np + p], ny);
         T v = gexp<T>(-dy * dy * k);
-        if (scale) v *= (T)amp[p];
+        if (scale) v *= par[2 * a.np + p];
         gy[q] = v;
     }
+}
+
+// bytes of the par block, padded to 16
+template <typename T>
+__host__ __device__ constexpr int gauss_par_bytes(int np) {
+    return (int)((3 * np * sizeof(T) + 15) / 16 * 16);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_gauss_source(Geo g, GaussArgs a, T *jx, T *jy, T *jz, int zero_xy) {
     extern __shared__ __align__(16) unsigned char gsm[];
-    double *amp = reinterpret_cast<double *>(gsm);  // [np]
-    T *gx = reinterpret_cast<T *>(amp + a.np);
+    T *par = reinterpret_cast<T *>(gsm);  // [3][np]
+    T *gx = reinterpret_cast<T *>(gsm + gauss_par_bytes<T>(a.np));
     T *gy = gx + a.np * GTX;
     const int x0 = blockIdx.x * GTX, y0 = blockIdx.y * GTY;
-    gauss_profiles<T>(g, a, x0, y0, true, gx, gy, amp);
+    gauss_params<T>(a, true, par);
+    __syncthreads();
+    gauss_profiles<T>(g, a, x0, y0, true, gx, gy, par);
     __syncthreads();
     const int tx = threadIdx.x % GTX, ty = threadIdx.x / GTX;
     T acc[GRY];
 #pragma unroll
     for (int r = 0; r < GRY; ++r) acc[r] = T(0);
+    // several sources in flight: the row profile of a source is one broadcast
+    // 16-byte load per four rows (FP32)
+#pragma unroll 4
     for (int p = 0; p < a.np; ++p) {
         const T xv = gx[p * GTX + tx];
         const T *yr = gy + p * GTY + ty * GRY;
+        if constexpr (sizeof(T) == 4) {
 #pragma unroll
-        for (int r = 0; r < GRY; ++r) acc[r] += yr[r] * xv;
+            for (int h = 0; h < GRY; h += 4) {
+                const float4 y4 = *reinterpret_cast<const float4 *>(yr + h);
+                acc[h + 0] += y4.x * xv;
+                acc[h + 1] += y4.y * xv;
+                acc[h + 2] += y4.z * xv;
+                acc[h + 3] += y4.w * xv;
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < GRY; ++r) acc[r] += yr[r] * xv;
+        }
     }
     const int i = x0 + tx;
     if (i >= g.nx) return;
@@ -177,15 +207,17 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_gauss_project(Geo g, GaussArgs a, const T *f, double *partials, int nblk) {
     extern __shared__ __align__(16) unsigned char gsm[];
     double *wsum = reinterpret_cast<double *>(gsm);  // [8 warps][np]
-    T *gx = reinterpret_cast<T *>(wsum + 8 * a.np);
+    T *par = reinterpret_cast<T *>(wsum + 8 * a.np);  // [3][np]
+    T *gx = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(par) + gauss_par_bytes<T>(a.np));
     T *gy = gx + a.np * GTX;
     const int tilesx = (g.nx + GTX - 1) / GTX, ntiles = tilesx * ((g.ny + GTY - 1) / GTY);
     const int tx = threadIdx.x % GTX, ty = threadIdx.x / GTX, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int q = threadIdx.x; q < 8 * a.np; q += blockDim.x) wsum[q] = 0.0;
+    gauss_params<T>(a, false, par);  // synchronised by the first tile's barrier
     for (int tile = blockIdx.x; tile < ntiles; tile += nblk) {
         const int x0 = (tile % tilesx) * GTX, y0 = (tile / tilesx) * GTY;
         __syncthreads();  // previous tile's profiles are consumed
-        gauss_profiles<T>(g, a, x0, y0, false, gx, gy, nullptr);
+        gauss_profiles<T>(g, a, x0, y0, false, gx, gy, par);
         __syncthreads();
         const int i = x0 + tx;
         T fv[GRY];
@@ -194,11 +226,25 @@ __global__ void __launch_bounds__(256) k_gauss_project(Geo g, GaussArgs a, const
             const int j = y0 + ty * GRY + r;
             fv[r] = (i < g.nx && j < g.ny) ? f[(int64_t)j * g.pitch + i] : T(0);
         }
+        // several sources in flight: their shuffle reductions are independent
+        // latency chains
+#pragma unroll 8
         for (int p = 0; p < a.np; ++p) {
             const T *yr = gy + p * GTY + ty * GRY;
             T s = T(0);
+            if constexpr (sizeof(T) == 4) {
 #pragma unroll
-            for (int r = 0; r < GRY; ++r) s += yr[r] * fv[r];
+                for (int h = 0; h < GRY; h += 4) {
+                    const float4 y4 = *reinterpret_cast<const float4 *>(yr + h);
+                    s += y4.x * fv[h + 0];
+                    s += y4.y * fv[h + 1];
+                    s += y4.z * fv[h + 2];
+                    s += y4.w * fv[h + 3];
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < GRY; ++r) s += yr[r] * fv[r];
+            }
             T v = s * gx[p * GTX + tx];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -272,7 +318,10 @@ int launch_scale_copy(const Geo &g, T sc, T *const in[3], T *const out[3], cudaS
 // per-warp sums (both in front of the profiles, so these stay 8-byte aligned)
 template <typename T>
 size_t gauss_smem(int np, bool project) {
-    return (size_t)np * (GTX + GTY) * sizeof(T) + (size_t)(project ? 8 : 1) * np * sizeof(double);
+    // [wsum: 8 np doubles, projection only][par, padded to 16 bytes][gx][gy]:
+    // the profiles start 16-byte aligned for 16-byte loads
+    return (size_t)np * (GTX + GTY) * sizeof(T) + (project ? (size_t)8 * np * sizeof(double) : 0) +
+           (size_t)gauss_par_bytes<T>(np);
 }
 
 template <typename T>
