@@ -497,8 +497,12 @@ cudaEvent_t *profile_events(fmx_grid *g, size_t n) {
     return p;
 }
 
+// pre (optional): work that step k needs first, enqueued on the stream the
+// TM set runs on (step 0: the grid's stream, before the fork, so both sets see it)
+typedef fmx_status (*StepPre)(fmx_grid *g, int k, cudaStream_t s);
+
 template <typename T>
-fmx_status fused_step(fmx_grid *g, int nsteps) {
+fmx_status fused_step(fmx_grid *g, int nsteps, StepPre pre = nullptr) {
     const fmx::Coef<T> c0 = make_coef<T>(g->co);
     // TE/TM kernels: the TE and TM chains touch disjoint components, so the TM
     // launches go to a second stream, forked from and joined back into the
@@ -506,6 +510,10 @@ fmx_status fused_step(fmx_grid *g, int nsteps) {
     bool two = false;
     if constexpr (sizeof(T) == 4)
         two = nsteps > 0 && !g->prof && fmx::fused2d_pol_supported(g->geo) && c0.c6 == 1.f / 6.f;
+    if (pre && nsteps > 0) {
+        fmx_status s = pre(g, 0, g->stream);
+        if (s != FMX_OK) return s;
+    }
     if (two) {
         cudaError_t e = cudaSuccess;
         if (!g->s_tm) e = cudaStreamCreateWithFlags(&g->s_tm, cudaStreamNonBlocking);
@@ -516,6 +524,10 @@ fmx_status fused_step(fmx_grid *g, int nsteps) {
         if (e != cudaSuccess) return cuda_fail(e, "TM stream fork");
     }
     for (int n = 0; n < nsteps; ++n) {
+        if (pre && n > 0) {
+            fmx_status s = pre(g, n, two ? g->s_tm : g->stream);
+            if (s != FMX_OK) return s;
+        }
         const fmx::Coef<T> c = step_coef<T>(g);
         const int nxt = 1 - g->cur;
         fmx::Fused2dArgs<T> a{};
@@ -1073,12 +1085,28 @@ static fmx::GaussSrc gauss_run_src(const fmx_grid *g, int64_t n) {
                          g->gauss_omega0, ((double)n + 0.5) * g->dt, g->gauss_width};
 }
 
+// the synthesis of step k of the running fmx_gauss_run (it writes j_z, read
+// by the TM set only, so it runs on the TM stream; step 0 also zeroes j_x, j_y)
+static thread_local int64_t t_gauss_n0 = 0;
+static fmx_status gauss_pre(fmx_grid *g, int k, cudaStream_t s) {
+    float *J[3] = {(float *)g->buf.J[0], (float *)g->buf.J[1], (float *)g->buf.J[2]};
+    g->launches += fmx::launch_gauss_source<float>(g->geo, gauss_run_src(g, t_gauss_n0 + k), J, k == 0, s);
+    return check_launch(g, "Gaussian source launch");
+}
+
 fmx_status fmx_gauss_run(fmx_grid *g, int64_t n0, int nsteps) {
     if (!g) return fail(FMX_EINVAL, "NULL grid");
     if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
     if (!g->buf.J[0]) return fail(FMX_ESTATE, "no J buffers bound");
     if (g->gauss_np < 1) return fail(FMX_ESTATE, "fmx_gauss_setup not called");
     if (nsteps < 0) return fail(FMX_EINVAL, "nsteps < 0");
+    if (g->engine == FMX_ENGINE_FUSED && g->p.precision == FMX_F32) {
+        // one fused run: the TE chain and the synthesis + TM chain overlap across steps
+        t_gauss_n0 = n0;
+        fmx_status s = fused_step<float>(g, nsteps, gauss_pre);
+        if (s == FMX_OK) g->steps += nsteps;
+        return s;
+    }
     for (int k = 0; k < nsteps; ++k) {
         const fmx::GaussSrc gs = gauss_run_src(g, n0 + k);
         if (g->p.precision == FMX_F64) {
