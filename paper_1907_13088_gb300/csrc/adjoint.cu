@@ -226,29 +226,47 @@ __global__ void __launch_bounds__(256) k_gauss_project(Geo g, GaussArgs a, const
             const int j = y0 + ty * GRY + r;
             fv[r] = (i < g.nx && j < g.ny) ? f[(int64_t)j * g.pitch + i] : T(0);
         }
-        // several sources in flight: their shuffle reductions are independent
-        // latency chains
-#pragma unroll 8
-        for (int p = 0; p < a.np; ++p) {
-            const T *yr = gy + p * GTY + ty * GRY;
-            T s = T(0);
-            if constexpr (sizeof(T) == 4) {
+        // the sources in chunks of 32: each lane forms its products for all 32
+        // (zero past np), then a reduce-scatter over the warp (halving
+        // exchanges, 31 shuffles) leaves lane l with the warp's sum for source
+        // p0 + l, which it adds to the warp's FP64 slot
+        for (int p0 = 0; p0 < a.np; p0 += 32) {
+            T v[32];
 #pragma unroll
-                for (int h = 0; h < GRY; h += 4) {
-                    const float4 y4 = *reinterpret_cast<const float4 *>(yr + h);
-                    s += y4.x * fv[h + 0];
-                    s += y4.y * fv[h + 1];
-                    s += y4.z * fv[h + 2];
-                    s += y4.w * fv[h + 3];
+            for (int i = 0; i < 32; ++i) {
+                const int p = p0 + i;
+                T s = T(0);
+                if (p < a.np) {
+                    const T *yr = gy + p * GTY + ty * GRY;
+                    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+                        for (int h = 0; h < GRY; h += 4) {
+                            const float4 y4 = *reinterpret_cast<const float4 *>(yr + h);
+                            s += y4.x * fv[h + 0];
+                            s += y4.y * fv[h + 1];
+                            s += y4.z * fv[h + 2];
+                            s += y4.w * fv[h + 3];
+                        }
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < GRY; ++r) s += yr[r] * fv[r];
+                    }
+                    s *= gx[p * GTX + tx];
                 }
-            } else {
-#pragma unroll
-                for (int r = 0; r < GRY; ++r) s += yr[r] * fv[r];
+                v[i] = s;
             }
-            T v = s * gx[p * GTX + tx];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) wsum[warp * a.np + p] += (double)v;
+            for (int r = 0; r < 5; ++r) {
+                const int o = 16 >> r;  // the half kept: upper when this lane's bit o is set
+                const bool up = (lane & o) != 0;
+#pragma unroll
+                for (int i = 0; i < o; ++i) {
+                    const T send = up ? v[i] : v[i + o];
+                    const T keep = up ? v[i + o] : v[i];
+                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                }
+            }
+            if (p0 + lane < a.np) wsum[warp * a.np + p0 + lane] += (double)v[0];
         }
     }
     __syncthreads();
