@@ -505,9 +505,36 @@ def cpu_baseline(E, B, J):
     core.step(p, E1, B1, J64, n)
     secs = time.perf_counter() - t0
     rate = NX * NY * n / secs
+    # the same oracle on one core, on a 1024^2 periodic sample (two steps)
+    core.threads(1)
+    try:
+        one, _, one_s = _oracle_sample_rate(1024, 2, 1)
+    finally:
+        core.threads(os.cpu_count() or 1)
     return {"value": round(rate / 1e9, 6), "unit": UNIT, "cores": used, "kind": "oracle",
             "sample": f"the full 4096x4096 workload, {n} steps after one sizing step, FP64 C oracle "
-                      f"({secs:.1f} s, OpenMP over rows)"}
+                      f"({secs:.1f} s, OpenMP over rows)",
+            "cpu_model": _cpu_model(),
+            "one_core": {"value": round(one / 1e9, 6), "unit": UNIT,
+                         "sample": f"1024x1024 periodic sample, 2 steps ({one_s:.1f} s)"}}
+
+
+def _cpu_model():
+    """The host CPU as /proc/cpuinfo names it (x86: model name; Arm: the
+    implementer and part numbers), with the architecture."""
+    import platform
+    info = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if ":" in line:
+                    k, v = (x.strip() for x in line.split(":", 1))
+                    info.setdefault(k, v)
+    except OSError:
+        pass
+    name = info.get("model name") or (
+        f"CPU implementer {info['CPU implementer']} part {info['CPU part']}" if "CPU part" in info else "")
+    return f"{platform.machine()} {name}".strip()
 
 
 def run_reference(args):
