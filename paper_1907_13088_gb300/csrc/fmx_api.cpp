@@ -1344,7 +1344,7 @@ struct fmx_batch {
     cudaStream_t stream = nullptr;
     int threads = 0, halo = 0, width = 0, bps = 1, sms = 1;
     size_t smem = 0;
-    // polarisation-split column-pair tiles (even n_x, unlumped), when instantiated
+    // polarisation-split column-pair tiles (unlumped grids), when instantiated
     bool pol_ok = false;
     int pwidth = 0, pbps = 1;
     size_t psmem = 0;

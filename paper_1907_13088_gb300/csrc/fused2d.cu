@@ -381,7 +381,9 @@ __global__ void __launch_bounds__(NT, 2)
 }
 
 // Batched step: a persistent grid-stride loop over (grid, strip, segment)
-// tiles of many independent grids (longest tiles first), one launch per step.
+// tiles of many independent grids (longest tiles first), one launch per step;
+// the batch runs its lumped grids here (the unlumped ones on the column-pair
+// tiles of fused2d_pol_batch.cu).
 template <int M, int P, bool HJ, int NT>
 __global__ void __launch_bounds__(NT, 2)
     k_fused2d_batch(const BatchGrid *__restrict__ grids, const BatchItem *__restrict__ items, int nitems, int parity) {
