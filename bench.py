@@ -473,6 +473,53 @@ def run_3d(args):
     print(json.dumps(line), flush=True)
 
 
+def run_res64(args):
+    """The 64 x 64 FP64 plane-wave case: 8 TM plane waves (|n| <= 8), no
+    current, no filter, the solve to a relative residual of 1e-13 every step
+    (Algorithm 1 on the staged engine), 200 steps; beside it the same run
+    with the Chebyshev residual mode.  The grid fits in L2: a latency case,
+    reported without a roofline."""
+    import numpy as np
+    import torch
+    from paper_1907_13088_gb300 import build, synth
+    build.build()
+    from paper_1907_13088_gb300 import fmx
+    shape, nsteps = (64, 64), 200
+    out = {}
+    for name, mode in (("algorithm1", fmx.FMX_ITER_RESIDUAL), ("chebyshev", fmx.FMX_ITER_CHEB_RESIDUAL)):
+        g = fmx.Grid(shape, with_current=False, precision=fmx.FMX_F64, iter_mode=mode, tol=1e-13, m_max=10000,
+                     courant=0.5, engine=fmx.FMX_ENGINE_STAGED)
+        E, B, _ = synth.tm_plane_waves(shape, g.dt, seed=1907001)
+        reps = []
+        for rep_ in range(args.warmup + 1):  # warm-up passes, then the timed one
+            g.set_fields(E, B)
+            s0 = g.diagnostics()["total_sweeps"]
+            l0 = g.launches
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.step(nsteps)
+            g.sync()
+            reps.append((time.perf_counter() - t0, g.diagnostics()["total_sweeps"] - s0, g.launches - l0))
+        out[name] = reps[-1]
+        g.close()
+    secs, sweeps, launches = out["algorithm1"]
+    value = 64 * 64 * nsteps / secs / 1e9
+    line = {
+        "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": 1, "steps": nsteps,
+        "warmup": args.warmup, "ms_per_step": round(secs / nsteps * 1e3, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "2D periodic 64x64 FP64, 8 TM plane waves |n|<=8 (seed 1907001), no current, "
+                               "no filter, residual 1e-13 every step (Algorithm 1), 200 steps, dt=0.5 dt_CFL",
+                   "sweeps_per_step": round(sweeps / nsteps, 2),
+                   "chebyshev_residual_mode": {"ms_per_step": round(out["chebyshev"][0] / nsteps * 1e3, 4),
+                                               "sweeps_per_step": round(out["chebyshev"][1] / nsteps, 2)},
+                   "timing": "host wall clock around the 200 steps, synchronised (each step reads the "
+                             "device residual back)"},
+        "roofline": None, "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def _oracle_sample_rate(n, nsteps, threads):
     """Runs the FP64 oracle on an n x n periodic sample of the workload;
     returns (cell-updates/s, threads used, seconds)."""
@@ -572,7 +619,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
-    ap.add_argument("--workload", choices=("2d4096", "batch256", "adjoint1024", "3d512"), default="2d4096")
+    ap.add_argument("--workload", choices=("2d4096", "batch256", "adjoint1024", "3d512", "res64"), default="2d4096")
     ap.add_argument("--n3d", type=int, default=512, help="cube side of the 3d512 workload (profiler captures only)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -585,6 +632,8 @@ def main():
         run_adjoint(args)
     elif args.workload == "3d512":
         run_3d(args)
+    elif args.workload == "res64":
+        run_res64(args)
     else:
         run_ours(args)
 
