@@ -146,3 +146,18 @@ def test_nci_rejects_bad_parameters_before_any_device_work(fmx):
     p = fmx.nci_params()
     assert fmx.fmx_nci_resonance(ctypes.byref(p), None, None, 16, None, None) == fmx.FMX_EINVAL
     assert fmx.fmx_nci_resonance(None, None, 16, 16, None, None) == fmx.FMX_EINVAL
+
+
+def test_current_profile_needs_a_bound_grid(fmx):
+    """fmx_set_current_profile checks its handle on the host: NULL grid ->
+    FMX_EINVAL, a grid not yet bound -> FMX_ESTATE (no device work)."""
+    import ctypes
+    p = fmx.make_params((16, 16), courant=0.5)
+    h = ctypes.c_void_p()
+    fmx.check(fmx.fmx_create(ctypes.byref(p), ctypes.byref(h), None))
+    try:
+        t = (ctypes.c_double * 2)(1.0, 0.5)
+        assert fmx.fmx_set_current_profile(None, t, 2) == fmx.FMX_EINVAL
+        assert fmx.fmx_set_current_profile(h, t, 2) == fmx.FMX_ESTATE
+    finally:
+        fmx.fmx_destroy(h)

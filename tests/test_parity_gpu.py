@@ -389,6 +389,11 @@ def test_current_time_profile(fmx, case):
     g = fmx.Grid(shape, precision=prec, engine=case["engine"], **case["kw"])
     g.set_fields(E, B)
     g.set_current(J)
+    import ctypes
+    bad = (ctypes.c_double * 2)(1.0, float("nan"))
+    assert fmx.fmx_set_current_profile(g.handle, bad, 2) == fmx.FMX_EINVAL
+    assert fmx.fmx_set_current_profile(g.handle, None, 3) == fmx.FMX_EINVAL
+    assert fmx.fmx_set_current_profile(g.handle, bad, -1) == fmx.FMX_EINVAL
     g.set_current_profile(table)
     g.step(nsteps)
     Eg, Bg, _ = g.get_fields()
