@@ -450,9 +450,15 @@ fmx_status staged_step(fmx_grid *g) {
         if (!resid) {  // Chebyshev, fixed m
             for (int it = 0; it < g->p.m; ++it) sweep();
         }
+        // residual mode: the first chunk as long as the previous step's solve (the
+        // next one usually needs about as many sweeps), then chunks of 8; sweeps
+        // past the stop are no-ops on the device
+        int chunk = g->last_sweeps > 8 ? g->last_sweeps : 8;
         for (;;) {
-            if (resid)
-                for (int q = 0; q < 8; ++q) sweep();
+            if (resid) {
+                for (int q = 0; q < chunk; ++q) sweep();
+                chunk = 8;
+            }
             s = check_launch(g, "residual sweep launch");
             if (s != FMX_OK) return s;
             cudaError_t e = cudaMemcpyAsync(&hs, g->st, sizeof(hs), cudaMemcpyDeviceToHost, g->stream);
