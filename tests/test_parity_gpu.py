@@ -217,6 +217,43 @@ def test_residual_mode_plane_waves_64(fmx):
     del errs
 
 
+@pytest.mark.parametrize("iter_mode", ["jacobi", "chebyshev"])
+@pytest.mark.parametrize("order", ["rough_first", "smooth_first"])
+def test_residual_mode_sweep_count_changes(fmx, iter_mode, order):
+    """Residual mode when the solve length changes from one step to the next:
+    rough fields (high-k content, eigenvalues of A near the Brillouin-zone
+    corner) need many more sweeps than smooth ones.  The host launches the
+    previous solve's count first, so after rough -> smooth the sweeps past the
+    stop must leave the state untouched, and after smooth -> rough further
+    chunks must follow.  Every step against the oracle: fields and sweeps."""
+    shape = (40, 36)
+    cheb = iter_mode == "chebyshev"
+    mode = fmx.FMX_ITER_CHEB_RESIDUAL if cheb else fmx.FMX_ITER_RESIDUAL
+    kw = dict(filter_passes=1, courant=0.8, tol=1e-12, m_max=5000)
+    rough = _inputs(shape, 17, np.float64)
+    smooth = _inputs(shape, 18, np.float64, smooth=True)
+    seq = [rough, smooth] if order == "rough_first" else [smooth, rough]
+    g = fmx.Grid(shape, with_current=True, precision=1, engine=1, iter_mode=mode, **kw)
+    counts = []
+    for E, B, J in seq + seq[:1]:
+        g.set_fields(E, B)
+        g.set_current(J)
+        g.step(1)
+        Eg, Bg, _ = g.get_fields()
+        Eo, Bo, rc, st = _oracle(shape, E, B, J, 1, cheb=cheb, residual=True, **kw)
+        assert rc == core.OK
+        assert_parity(np.asarray(Eg, np.float64), np.asarray(Bg, np.float64), Eo, Bo, TOL64,
+                      f"residual {iter_mode} {order} step {len(counts)}")
+        d = g.diagnostics()
+        assert d["last_sweeps"] == st["last_sweeps"], (d["last_sweeps"], st["last_sweeps"])
+        counts.append(d["last_sweeps"])
+    # the two inputs need different solve lengths (Algorithm 1: 78 and 33
+    # sweeps; Chebyshev: 26 and 24), so one order runs sweeps past the stop
+    # and the other a further chunk
+    assert counts[0] != counts[1], counts
+    assert counts[2] == counts[0]
+
+
 def test_residual_mode_noconv(fmx):
     shape = (16, 16)
     E, B, J = _inputs(shape, 5, np.float64)
