@@ -60,7 +60,7 @@ typedef enum {
     FMX_ECUDA = 4,       /* a CUDA runtime call failed                        */
     FMX_ETIMEOUT = 5,    /* a bounded device-side wait gave up                */
     FMX_ESTATE = 6,      /* call out of order (e.g. stepping before fmx_bind) */
-    FMX_EUNSUPPORTED = 7 /* combination this build does not provide           */
+    FMX_EUNSUPPORTED = 7 /* combination the library does not provide         */
 } fmx_status;
 
 enum { FMX_F32 = 0, FMX_F64 = 1 };                        /* storage and sweep precision */
