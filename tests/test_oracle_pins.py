@@ -116,11 +116,15 @@ def test_3d_dispersion_converged():
     E[2] = 0.3 * np.sin(2 * np.pi * (mx * i / 12 + my * j / 10 + mz * (k + 0.5) / 8))
     seq = []
     for _ in range(3):
-        seq.append(np.fft.fftn(B[0])[mz, my, mx])
+        seq.append([np.fft.fftn(B[c])[mz, my, mx] for c in range(3)])
         E, B, rc, _ = core.step(p, E, B, None, 1)
-    w = math.acos(((seq[0] + seq[2]) / (2 * seq[1])).real) / p.time_step()
     kv = (2 * np.pi * mx / (12 * 1.0), 2 * np.pi * my / (10 * 0.8), 2 * np.pi * mz / (8 * 1.2))
-    assert abs(w - spectral.omega_converged(p, kv)) / w < 1e-11
+    # every component of B: a wrong term may move only a curl-free part of E,
+    # which a single component of curl E can miss
+    for c in range(3):
+        f0, f1, f2 = (seq[n][c] for n in range(3))
+        w = math.acos(((f0 + f2) / (2 * f1)).real) / p.time_step()
+        assert abs(w - spectral.omega_converged(p, kv)) / w < 1e-11, c
 
 
 def test_plane_wave_sum_phase_advance_200_steps():
@@ -423,3 +427,58 @@ def test_residual_mode_zero_source_and_noconv():
     rng = np.random.default_rng(1)
     _, rc, sw, _ = core.solve(p, rng.standard_normal(p.array_shape))
     assert rc == core.ENOCONV and sw == 3
+
+
+def _lambda_tm(p, kx, ky):
+    """Symbol of A_zz (Eqs. matrixA_1st_2d..last_2d) with Dbar_aa -> -4 sin^2(k_a d_a / 2):
+    (2/3)(1 - s_x) S_x + (2/3)(1 - s_y) S_y - (4/9)(1 - s_x - s_y) S_x S_y,
+    s_a = (c dt / d_a)^2, S_a = sin^2(k_a d_a / 2)."""
+    dt = p.time_step()
+    sx, sy = (p.c * dt / p.d[0]) ** 2, (p.c * dt / p.d[1]) ** 2
+    ax, ay = math.sin(kx * p.d[0] / 2) ** 2, math.sin(ky * p.d[1] / 2) ** 2
+    return 2 / 3 * (1 - sx) * ax + 2 / 3 * (1 - sy) * ay - 4 / 9 * (1 - sx - sy) * ax * ay
+
+
+@pytest.mark.parametrize("shape,d,courant,mode,tol", [
+    ((20, 16), (1.0, 1.0, 1.0), 0.9, (3, 5), 1e-9),
+    ((24, 20), (1.0, 0.7, 1.0), 0.5, (9, 7), 1e-12),
+    ((32, 32), (1.0, 1.0, 1.0), 0.3, (16, 16), 1e-11),
+    ((18, 30), (0.8, 1.1, 1.0), 1.0, (2, 11), 1e-7)])
+def test_residual_stop_on_one_eigenmode(shape, d, courant, mode, tol):
+    """Residual mode (Sec. 2.2.1 stop rule, read as the relative L2 norm of
+    the update): for dE' a single TM mode, A acts as the scalar lambda_z(k),
+    the update of sweep s is lambda^s dE', so the solve stops at the first s
+    with |lambda|^s <= tol and reports |lambda|^s."""
+    nx, ny = shape
+    p = core.Params(shape=shape, d=d, courant=courant, residual=True, tol=tol, m_max=100000)
+    kx, ky = 2 * math.pi * mode[0] / (nx * d[0]), 2 * math.pi * mode[1] / (ny * d[1])
+    dEp = np.zeros(p.array_shape)
+    dEp[2, 0] = np.cos(2 * math.pi * (mode[0] * np.arange(nx)[None, :] / nx + mode[1] * np.arange(ny)[:, None] / ny))
+    lam = abs(_lambda_tm(p, kx, ky))
+    q = math.log(tol) / math.log(lam)
+    assert 0.05 < q - math.floor(q) < 0.95  # the case is not at a rounding boundary
+    dE, rc, sw, r = core.solve(p, dEp)
+    assert rc == core.OK and sw == math.ceil(q), (sw, q)
+    assert abs(r - lam ** sw) <= 1e-6 * lam ** sw + 1e-14
+    np.testing.assert_allclose(dE, dEp / (1 - _lambda_tm(p, kx, ky)), rtol=0, atol=10 * tol)
+
+
+@pytest.mark.parametrize("shape,kw", [((12, 10), dict(m=4, filter_passes=3)),
+                                      ((6, 5, 7), dict(m=2, filter_passes=1, d=(1.0, 0.8, 1.2))),
+                                      ((20,), dict(m=3)),
+                                      ((9, 8), dict(residual=True, tol=1e-14))])
+def test_uniform_current_closed_form(shape, kw):
+    """A uniform current with no fields: every difference operator vanishes,
+    so Ampere's law in Gaussian units (Sec. 2) leaves dE/dt = -4 pi j exactly,
+    E^n = -4 pi n dt j and B = 0, for any m, filter or solve mode (the
+    binomial filter keeps constants)."""
+    p = core.Params(shape=shape, courant=0.7, **kw)
+    jv = (0.3, -1.1, 0.7)
+    J = np.zeros(p.array_shape)
+    for c in range(3):
+        J[c] = jv[c]
+    E, B, rc, _ = core.step(p, np.zeros(p.array_shape), np.zeros(p.array_shape), J, 3)
+    assert rc == core.OK
+    for c in range(3):
+        np.testing.assert_allclose(E[c], -3 * 4 * math.pi * p.time_step() * jv[c], rtol=1e-14, atol=0)
+    assert np.all(B == 0)
