@@ -98,3 +98,38 @@ def test_library_interval_matches_oracle(shape, courant, d):
         fmx.fmx_destroy(h)
     olo, ohi = spectral.a_interval(core.Params(shape=shape, courant=courant, d=d))
     assert abs(lo.value - olo) < 1e-13 and abs(hi.value - ohi) < 1e-13
+
+
+CHEB_MUTATIONS = {
+    "rho_recurrence": ("const double rho_new = 1.0 / (2.0 * sig - rho);",
+                       "const double rho_new = 1.0 / (sig - rho);"),
+    "first_step_scale": ("c2 = 1.0 / theta;", "c2 = 1.0 / delta;"),
+    "momentum_weight": ("c1 = rho_new * rho;", "c1 = rho_new;"),
+    "step_weight": ("c2 = 2.0 * rho_new / delta;", "c2 = rho_new / delta;"),
+    # the interval of A taken for that of M = 1 - A (swapping the interval's
+    # ends is no mistake: delta and every rho change sign together and the
+    # recurrence's coefficients stay the same)
+    "interval_of_A": ("const double al = 1.0 - p->cheb_hi, be = 1.0 - p->cheb_lo;",
+                      "const double al = p->cheb_lo, be = p->cheb_hi;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CHEB_MUTATIONS))
+def test_chebyshev_planted_mistake_is_caught(name, tmp_path):
+    """A plausible mistake in the C recurrence must break the per-wavevector
+    error-polynomial pin (the mutated copy is compiled to a temporary
+    directory; the oracle under test is not touched)."""
+    old, new = CHEB_MUTATIONS[name]
+    src = core.source_text()
+    assert src.count(old) == 1, name
+    lib = core.compile_variant(src.replace(old, new), str(tmp_path / "libmut.so"))
+    caught = False
+    with core.using_library(lib):
+        for shape, courant in (((16, 12), 0.5), ((8, 6, 5), 0.6)):
+            for m in (2, 5):
+                p = core.Params(shape=shape, courant=courant, m=m, cheb=True)
+                b = synth.random_fields(shape, seed=70 + m)[0]
+                x, rc, sweeps, _ = core.solve(p, b)
+                if rc != 0 or not np.all(np.isfinite(x)) or rel_l2(x, _per_k_expected(p, b, m)) >= 1e-12:
+                    caught = True
+    assert caught, f"mutation {name} passed the error-polynomial pin"
