@@ -529,10 +529,13 @@ fmx_status fused_step(fmx_grid *g, int nsteps, StepPre pre = nullptr) {
         if (e == cudaSuccess) e = cudaStreamWaitEvent(g->s_tm, g->ev_fork, 0);
         if (e != cudaSuccess) return cuda_fail(e, "TM stream fork");
     }
+    // after the fork every exit goes through the join below, so that work
+    // enqueued later on the grid's stream waits for the TM launches already made
+    fmx_status st = FMX_OK;
     for (int n = 0; n < nsteps; ++n) {
         if (pre && n > 0) {
-            fmx_status s = pre(g, n, two ? g->s_tm : g->stream);
-            if (s != FMX_OK) return s;
+            st = pre(g, n, two ? g->s_tm : g->stream);
+            if (st != FMX_OK) break;
         }
         const fmx::Coef<T> c = step_coef<T>(g);
         const int nxt = 1 - g->cur;
@@ -565,17 +568,22 @@ fmx_status fused_step(fmx_grid *g, int nsteps, StepPre pre = nullptr) {
             if (ev) cudaEventRecord(ev[1], g->stream), cudaEventRecord(ev[2], g->stream);
             g->prof_kinds = 1;
         }
-        if (nl < 0) return fail(FMX_EUNSUPPORTED, "fused 2D kernel: configuration not instantiated");
+        if (nl < 0) {
+            st = fail(FMX_EUNSUPPORTED, "fused 2D kernel: configuration not instantiated");
+            break;
+        }
         g->launches += nl;
         g->cur = nxt;
+        g->steps += 1;
         g->last_sweeps = g->p.m;
         g->total_sweeps += g->p.m;
     }
     if (two) {
         cudaError_t e = cudaEventRecord(g->ev_join, g->s_tm);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(g->stream, g->ev_join, 0);
-        if (e != cudaSuccess) return cuda_fail(e, "TM stream join");
+        if (e != cudaSuccess && st == FMX_OK) st = cuda_fail(e, "TM stream join");
     }
+    if (st != FMX_OK) return st;
     return check_launch(g, "fused step launch");
 }
 
@@ -861,9 +869,7 @@ fmx_status fmx_step(fmx_grid *g, int nsteps) {
     if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
     if (nsteps < 0) return fail(FMX_EINVAL, "nsteps < 0");
     if (g->engine == FMX_ENGINE_FUSED) {
-        fmx_status s = g->p.precision == FMX_F64 ? fused_step<double>(g, nsteps) : fused_step<float>(g, nsteps);
-        if (s == FMX_OK) g->steps += nsteps;
-        return s;
+        return g->p.precision == FMX_F64 ? fused_step<double>(g, nsteps) : fused_step<float>(g, nsteps);
     }
     for (int n = 0; n < nsteps; ++n) {
         fmx_status s = g->p.precision == FMX_F64 ? staged_step<double>(g) : staged_step<float>(g);
@@ -1109,9 +1115,7 @@ fmx_status fmx_gauss_run(fmx_grid *g, int64_t n0, int nsteps) {
     if (g->engine == FMX_ENGINE_FUSED && g->p.precision == FMX_F32) {
         // one fused run: the TE chain and the synthesis + TM chain overlap across steps
         t_gauss_n0 = n0;
-        fmx_status s = fused_step<float>(g, nsteps, gauss_pre);
-        if (s == FMX_OK) g->steps += nsteps;
-        return s;
+        return fused_step<float>(g, nsteps, gauss_pre);
     }
     for (int k = 0; k < nsteps; ++k) {
         const fmx::GaussSrc gs = gauss_run_src(g, n0 + k);
