@@ -326,18 +326,23 @@ size_t fmx_batch_workspace_bytes(const fmx_batch *b);
 /* Lends the batch the buffers of its n grids (bufs[i] as in fmx_bind, set 0
  * and set 1 required, J all NULL or all set in every grid) and a
  * 256-byte-aligned workspace; builds the work list with the automatic tile
- * rows.  Errors: FMX_EINVAL, FMX_ECUDA. */
+ * rows.  The batch counts as bound only once the work list is on the device.
+ * Errors: FMX_EINVAL, FMX_ECUDA. */
 fmx_status fmx_batch_bind(fmx_batch *b, const fmx_buffers *bufs, void *work, size_t work_bytes);
 
 /* Copy grid i's components in or out of its current state set (as
- * fmx_set_fields / fmx_get_fields; get synchronises). */
+ * fmx_set_fields / fmx_get_fields; get synchronises).  mask: FMX_E and FMX_B
+ * bits only; every component the mask names needs a pointer.  Errors:
+ * FMX_EINVAL (bad index, mask or NULL pointer), FMX_ESTATE (not bound),
+ * FMX_ECUDA. */
 fmx_status fmx_batch_set_fields(fmx_batch *b, int i, unsigned mask, const void *const *src, int where);
 fmx_status fmx_batch_get_fields(fmx_batch *b, int i, unsigned mask, void *const *dst, int where);
 
 /* Rows per tile segment: rows > 0 caps every grid's segment at that many
  * rows; 0 selects the automatic choice.  Rebuilds the work list and drops
  * the captured graphs.  The tile's row extent changes only which rows are
- * recomputed as warm-up, never a result. */
+ * recomputed as warm-up, never a result.  A failed rebuild (FMX_EINVAL when
+ * the work list outgrows the workspace, FMX_ECUDA) unbinds the batch. */
 fmx_status fmx_batch_set_rows(fmx_batch *b, int rows);
 
 /* Autotuner: times each candidate row extent (automatic, 1024, 512, 256, 128,

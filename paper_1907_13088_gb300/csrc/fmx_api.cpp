@@ -1578,7 +1578,7 @@ fmx_status fmx_batch_bind(fmx_batch *b, const fmx_buffers *bufs, void *work, siz
             G.J[c] = (const float *)bufs[i].J[c];
         }
     }
-    b->hj = hj && b->passes >= 0;
+    b->hj = hj;
     if (fmx::fused2d_batch_geometry(b->m, b->hj ? b->passes : 0, b->hj, &b->threads, &b->halo, &b->width, &b->smem,
                                     &b->bps) != 0)
         return fail(FMX_EUNSUPPORTED, "no batched kernel for m = %d, passes = %d", b->m, b->passes);
@@ -1597,8 +1597,10 @@ fmx_status fmx_batch_bind(fmx_batch *b, const fmx_buffers *bufs, void *work, siz
     b->max_items = (work_bytes - align_up(sizeof(fmx::BatchGrid) * b->n, kAlign)) / sizeof(fmx::BatchItem);
     b->parity = 0;
     b->launches = b->steps = 0;
-    b->bound = true;
-    return batch_build(b);
+    // bound only once the work list is on the device
+    const fmx_status s = batch_build(b);
+    b->bound = s == FMX_OK;
+    return s;
 }
 
 fmx_status fmx_batch_set_fields(fmx_batch *b, int i, unsigned mask, const void *const *src, int where) {
@@ -1609,6 +1611,7 @@ fmx_status fmx_batch_set_fields(fmx_batch *b, int i, unsigned mask, const void *
     const size_t sp = (size_t)G.g.nx * 4, dp = (size_t)G.g.pitch * 4;
     for (int c = 0; c < 6; ++c) {
         if (!(mask & (1u << c))) continue;
+        if (!src[c]) return fail(FMX_EINVAL, "src[%d] is NULL", c);
         void *dst = (void *)(c < 3 ? G.E[b->parity][c] : G.B[b->parity][c - 3]);
         cudaError_t e = cudaMemcpy2DAsync(dst, dp, src[c], sp, sp, (size_t)G.g.ny, cudaMemcpyDefault, b->stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2DAsync");
@@ -1623,11 +1626,13 @@ fmx_status fmx_batch_set_fields(fmx_batch *b, int i, unsigned mask, const void *
 fmx_status fmx_batch_get_fields(fmx_batch *b, int i, unsigned mask, void *const *dst, int where) {
     if (!b || !dst || i < 0 || i >= b->n) return fail(FMX_EINVAL, "bad arguments");
     if (!b->bound) return fail(FMX_ESTATE, "batch not bound");
+    if (mask & ~(unsigned)(FMX_E | FMX_B)) return fail(FMX_EINVAL, "mask holds bits other than E and B");
     (void)where;
     const fmx::BatchGrid &G = b->grids[i];
     const size_t dpch = (size_t)G.g.nx * 4, sp = (size_t)G.g.pitch * 4;
     for (int c = 0; c < 6; ++c) {
         if (!(mask & (1u << c))) continue;
+        if (!dst[c]) return fail(FMX_EINVAL, "dst[%d] is NULL", c);
         const void *src = c < 3 ? G.E[b->parity][c] : G.B[b->parity][c - 3];
         cudaError_t e = cudaMemcpy2DAsync(dst[c], dpch, src, sp, dpch, (size_t)G.g.ny, cudaMemcpyDefault, b->stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2DAsync");
@@ -1641,7 +1646,10 @@ fmx_status fmx_batch_set_rows(fmx_batch *b, int rows) {
     if (!b || rows < 0) return fail(FMX_EINVAL, "bad arguments");
     if (!b->bound) return fail(FMX_ESTATE, "batch not bound");
     b->rows_policy = rows;
-    return batch_build(b);
+    // a failed rebuild leaves descriptors and work list out of step: unbind
+    const fmx_status s = batch_build(b);
+    if (s != FMX_OK) b->bound = false;
+    return s;
 }
 
 fmx_status fmx_batch_step(fmx_batch *b, int nsteps) {
