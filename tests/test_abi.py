@@ -117,8 +117,27 @@ def test_batch_validation(fmx):
     arr = (fmx.fmx_params * 2)(*good)
     h = ctypes.c_void_p()
     assert fmx.fmx_batch_create(arr, 2, ctypes.byref(h)) == fmx.FMX_OK
-    assert fmx.fmx_batch_workspace_bytes(h) > 0
+    wb = fmx.fmx_batch_workspace_bytes(h)
+    assert wb > 0
+    # not bound yet: every call that needs the buffers refuses without device work
+    assert fmx.fmx_batch_items(h) == 0 and fmx.fmx_batch_launch_count(h) == 0
+    assert fmx.fmx_batch_step(h, 1) == fmx.FMX_ESTATE
+    assert fmx.fmx_batch_set_rows(h, 64) == fmx.FMX_ESTATE
+    assert fmx.fmx_batch_tune(h, 4, None) == fmx.FMX_ESTATE
+    ptrs = (ctypes.c_void_p * 6)()
+    assert fmx.fmx_batch_get_fields(h, 0, fmx.FMX_E, ptrs, fmx.FMX_HOST) == fmx.FMX_ESTATE
+    assert fmx.fmx_batch_set_fields(h, 0, fmx.FMX_E, ptrs, fmx.FMX_HOST) == fmx.FMX_ESTATE
+    assert fmx.fmx_batch_get_fields(h, 2, fmx.FMX_E, ptrs, fmx.FMX_HOST) == fmx.FMX_EINVAL  # no grid 2
+    # bind's argument checks come before any device work (the pointers are
+    # never dereferenced on these paths)
+    bufs = (fmx.fmx_buffers * 2)()
+    fake = ctypes.c_void_p(1 << 20)
+    assert fmx.fmx_batch_bind(h, bufs, ctypes.c_void_p(256 + 16), wb) == fmx.FMX_EINVAL  # misaligned workspace
+    assert fmx.fmx_batch_bind(h, bufs, fake, wb - 1) == fmx.FMX_EINVAL  # too small
+    assert fmx.fmx_batch_bind(h, bufs, fake, wb) == fmx.FMX_EINVAL  # NULL field buffers
+    assert fmx.fmx_batch_step(h, 1) == fmx.FMX_ESTATE  # a failed bind leaves it unbound
     fmx.fmx_batch_destroy(h)
+    assert fmx.fmx_batch_create(arr, 0, ctypes.byref(h)) == fmx.FMX_EINVAL
     bad = [fmx.make_params((64, 40), courant=0.5, stream=stream), fmx.make_params((33, 70), m=3, stream=stream)]
     assert fmx.fmx_batch_create((fmx.fmx_params * 2)(*bad), 2, ctypes.byref(h)) == fmx.FMX_EINVAL
     nostream = [fmx.make_params((64, 40), courant=0.5)]
@@ -127,6 +146,11 @@ def test_batch_validation(fmx):
     assert fmx.fmx_batch_create((fmx.fmx_params * 1)(*cfl), 1, ctypes.byref(h)) == fmx.FMX_ECFL
     f64 = [fmx.make_params((64, 40), precision=1, stream=stream)]
     assert fmx.fmx_batch_create((fmx.fmx_params * 1)(*f64), 1, ctypes.byref(h)) == fmx.FMX_EINVAL
+    for kw in (dict(iter_mode=fmx.FMX_ITER_RESIDUAL), dict(filter_passes=1, filter_target=fmx.FMX_FILTER_FIELDS)):
+        one = [fmx.make_params((64, 40), stream=stream, **kw)]
+        assert fmx.fmx_batch_create((fmx.fmx_params * 1)(*one), 1, ctypes.byref(h)) == fmx.FMX_EINVAL, kw
+    three_d = [fmx.make_params((16, 16, 16), stream=stream)]
+    assert fmx.fmx_batch_create((fmx.fmx_params * 1)(*three_d), 1, ctypes.byref(h)) == fmx.FMX_EINVAL
 
 
 def test_nci_rejects_bad_parameters_before_any_device_work(fmx):
