@@ -126,3 +126,20 @@ def test_batch_with_current(fmx):
         Eo, Bo, _, _ = core.step(core.Params(shape=sh, courant=cf, m=4, filter_passes=3, coef_f32=True),
                                  E.astype(np.float64), B.astype(np.float64), J.astype(np.float64), 5)
         assert_parity(Eg, Bg, Eo, Bo, TOL32, f"batch+current grid {i}")
+
+
+def test_batch_failed_rebuild_unbinds(fmx):
+    """A work list that outgrows the workspace (one row per segment: 161
+    tiles, where the workspace holds the 32-row bound of 21) is refused before
+    anything is uploaded or launched, and leaves the batch unbound: the next
+    step reports FMX_ESTATE."""
+    b = fmx.Batch(SHAPES[:2], COURANT[:2], m=4)
+    n0 = b.launches
+    with pytest.raises(fmx.FmxError) as ei:
+        b.set_rows(1)
+    assert ei.value.status == fmx.FMX_EINVAL
+    with pytest.raises(fmx.FmxError) as ei:
+        b.step(1)
+    assert ei.value.status == fmx.FMX_ESTATE
+    assert b.launches == n0
+    b.close()
