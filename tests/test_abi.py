@@ -185,3 +185,14 @@ def test_current_profile_needs_a_bound_grid(fmx):
         assert fmx.fmx_set_current_profile(h, t, 2) == fmx.FMX_ESTATE
     finally:
         fmx.fmx_destroy(h)
+
+
+def test_resource_report_kernel_names():
+    """The ptxas resource report names kernels by their short name with
+    template arguments (enum casts and anonymous namespaces dropped)."""
+    from paper_1907_13088_gb300.build import _short
+    assert _short("(anonymous namespace)::k_nci_best((anonymous namespace)::NciCoef, double const*, double*)") \
+        == "k_nci_best"
+    assert _short("void fmx::pol2d::k_pol2d<(fmx::pol2d::Pol)0, 4, 3, true, 128>(fmx::Fused2dArgs<float>, "
+                  "fmx::Geo, fmx::pol2d::Coef2, int, int, int)") == "k_pol2d<0, 4, 3, true, 128>"
+    assert _short("void fmx::(anonymous namespace)::k3_sweep2<true>(fmx::Geo, float const*)") == "k3_sweep2<true>"
