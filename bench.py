@@ -41,6 +41,15 @@ WORKLOAD = ("2D periodic 4096x4096 FP32 (FP64 reductions), dt=0.5 dt_CFL, power-
             "static solenoidal J (curl of Gaussian-spectrum potential, width 16), 3-pass binomial current "
             "filter every step, m=4 sweeps")
 FALLBACK_HBM_GBS = 6800.0
+# FP32 work of one 3D cell-step with the stencils as written, one FMA (2 flops)
+# per tap: the 1-pass filter, 3 axes x 3 taps x 3 components (54); the source,
+# per component two terms of a 3-tap average differenced over 2 points plus the
+# current (3 x 26 = 78); each sweep, per component the 9-tap diagonal block of
+# A, its two 12-tap cross terms and the add of dE' (3 x 67 = 201; four sweeps
+# 804); the E update (3); Faraday, 2 terms x 2 taps x 3 components (24)
+FLOPS_PER_CELL_STEP_3D = 54 + 78 + 4 * 201 + 3 + 24
+# FP32 FMA peak from the unit counts and clock: 152 SMs x 128 lanes x 2 flops x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def _dist():
@@ -79,6 +88,15 @@ def _peaks():
         except Exception:
             pass
     return FALLBACK_HBM_GBS, "fallback (6.8 TB/s, no MEASURED_PEAKS.json)"
+
+
+def alu_roofline(cells, seconds_per_step, flops_per_cell_step=FLOPS_PER_CELL_STEP_3D):
+    """FP32 arithmetic achieved against the FMA peak (the 3D step's flops per
+    byte, 963 / 60, lie above the ridge 80.5 TFLOP/s / 6.78 TB/s)."""
+    achieved = flops_per_cell_step * cells / seconds_per_step / 1e12
+    return {"bound": "alu", "achieved": round(achieved, 2), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+            "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "flops_per_cell_step": flops_per_cell_step,
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (unit counts and maximum SM clock)"}
 
 
 def _ncu_traffic(kernel_name):
@@ -467,7 +485,8 @@ def run_3d(args):
                    "engine": "staged" if g.launches - l0 > args.steps else "fused", "input_generation_s": round(gen_s, 1)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None, "kernel": "whole step",
-                     "peak_source": peak_src, "bytes_per_cell_step": BYTES_PER_CELL},
+                     "peak_source": peak_src, "bytes_per_cell_step": BYTES_PER_CELL,
+                     "alu": alu_roofline(cells, ms / 1e3 / args.steps)},
         "gpu_launches": int(g.launches - l0), "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
