@@ -960,8 +960,10 @@ fmx_status fmx_sync(fmx_grid *g) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "pending CUDA error");
     if (g->bound && g->st) {
+        // on the grid's own stream: the legacy default stream may hold other work
         fmx::DevStatus hs;
-        e = cudaMemcpy(&hs, g->st, sizeof(hs), cudaMemcpyDeviceToHost);
+        e = cudaMemcpyAsync(&hs, g->st, sizeof(hs), cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
         if (e != cudaSuccess) return cuda_fail(e, "status read-back");
         if (hs.err) return fail((fmx_status)hs.err, "device reported status %d", hs.err);
     }
