@@ -192,9 +192,15 @@ fmx_status fmx_set_current(fmx_grid *g, const void *const *src, int where);
 fmx_status fmx_set_current_profile(fmx_grid *g, const double *table, int len);
 
 /* Enqueues nsteps full steps (1..6 above) on the stream.  Fixed mode never
- * synchronises.  Residual mode reads the device residual back every few
- * sweeps (synchronising) and returns FMX_ENOCONV if a solve reaches m_max.
- * Errors: FMX_ESTATE, FMX_EINVAL (nsteps < 0), FMX_ECUDA, FMX_ENOCONV. */
+ * synchronises.  Residual mode reads the device residual back once per chunk
+ * of sweeps (synchronising; the first chunk of a step is as long as the
+ * previous step's solve, sweeps past the stop do nothing) and returns
+ * FMX_ENOCONV if a solve reaches m_max.  On an error the steps enqueued
+ * before it stand and are counted (fmx_diagnostics' steps); the state is
+ * that after the last of them, except after FMX_ENOCONV, where the failing
+ * step's E update and Faraday update have been applied with the unconverged
+ * solve.  Errors: FMX_ESTATE, FMX_EINVAL (nsteps < 0), FMX_ECUDA,
+ * FMX_ENOCONV. */
 fmx_status fmx_step(fmx_grid *g, int nsteps);
 
 /* Applies `passes` binomial passes along every active axis to the
