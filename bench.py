@@ -631,7 +631,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def main():
+def _parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3000)
@@ -640,6 +640,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--workload", choices=("2d4096", "batch256", "adjoint1024", "3d512", "res64"), default="2d4096")
     ap.add_argument("--n3d", type=int, default=512, help="cube side of the 3d512 workload (profiler captures only)")
+    return ap
+
+
+def main():
+    ap = _parser()
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

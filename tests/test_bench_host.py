@@ -23,3 +23,53 @@ def test_alu_roofline_of_the_3d_step():
     assert abs(r["frac"] - r["achieved"] / b.FP32_PEAK_TFLOPS) < 1e-3
     # above the ridge: flops per algorithmic byte exceed peak flops per HBM byte
     assert b.FLOPS_PER_CELL_STEP_3D / b.BYTES_PER_CELL > b.FP32_PEAK_TFLOPS * 1e12 / (6779.4e9)
+
+
+def _commands():
+    """Command lines quoted in the profile summaries (continuations joined)."""
+    out = []
+    pdir = os.path.join(ROOT, "profiles")
+    for name in sorted(os.listdir(pdir)):
+        if not name.endswith(".md"):
+            continue
+        lines = open(os.path.join(pdir, name)).read().splitlines()
+        buf = ""
+        for line in lines:
+            t = line.strip()
+            if buf:
+                buf += " " + t.rstrip("\\").strip()
+                if not t.endswith("\\"):
+                    out.append((name, buf))
+                    buf = ""
+            elif t.startswith(("python ", "ncu ")):
+                if t.endswith("\\"):
+                    buf = t.rstrip("\\").strip()
+                else:
+                    out.append((name, t))
+    return out
+
+
+def test_profile_commands_run_committed_files():
+    """Every command a profile summary quotes names a bench.py option set the
+    parser accepts, an existing ncu_report mode, or the build module's
+    resource report: the summaries stay reproducible from committed files."""
+    import shlex
+    b = _bench()
+    from paper_1907_13088_gb300 import build, ncu_report
+    cmds = _commands()
+    assert len(cmds) >= 8
+    seen_bench = 0
+    for name, cmd in cmds:
+        words = shlex.split(cmd)
+        if "bench.py" in words:
+            args = words[words.index("bench.py") + 1:]
+            b._parser().parse_args(args)  # raises SystemExit on an unknown option
+            seen_bench += 1
+        if "paper_1907_13088_gb300.ncu_report" in words:
+            mode = words[words.index("paper_1907_13088_gb300.ncu_report") + 1]
+            assert hasattr(ncu_report, mode), (name, mode)
+        if "paper_1907_13088_gb300.build" in words:
+            assert "--resources" in words and hasattr(build, "resources"), (name, cmd)
+        if words[0] == "ncu" and "-i" not in words:
+            assert "--clock-control" in words and words[words.index("--clock-control") + 1] == "none", (name, cmd)
+    assert seen_bench >= 5
