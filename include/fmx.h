@@ -216,10 +216,12 @@ fmx_status fmx_filter(fmx_grid *g, unsigned mask, int passes);
 fmx_status fmx_get_fields(fmx_grid *g, unsigned mask, void *const *dst, int where);
 
 /* Computes the FP64 diagnostics of the current state.  Synchronises.
- * Errors: FMX_ESTATE, FMX_ECUDA. */
+ * Errors: FMX_EINVAL (NULL), FMX_ESTATE, FMX_ECUDA. */
 fmx_status fmx_diagnostics(fmx_grid *g, fmx_diag *out);
 
-/* Waits for the grid's stream and returns any latched device status. */
+/* Waits for the grid's stream and returns any latched device status.
+ * Errors: FMX_EINVAL (NULL), FMX_ECUDA (a failed or pending CUDA call), or
+ * the status a kernel latched in the grid's status word. */
 fmx_status fmx_sync(fmx_grid *g);
 
 /* The FMX_NCOEF scalar factors the kernels multiply by, after rounding to
@@ -233,7 +235,7 @@ fmx_status fmx_sync(fmx_grid *g);
  * for entries 4..13.  Host-only; returns FMX_EINVAL if n < FMX_NCOEF. */
 fmx_status fmx_coefficients(const fmx_grid *g, double *out, int n);
 
-/* dt in use (after courant * dt_CFL). */
+/* dt in use (after courant * dt_CFL); 0 for a NULL handle. */
 double fmx_time_step(const fmx_grid *g);
 
 /* Chebyshev modes: the interval [lo, hi] taken to hold the eigenvalues of A --
@@ -326,7 +328,8 @@ typedef struct fmx_batch fmx_batch;
  * FMX_EUNSUPPORTED (an (m, passes) pair without a batched kernel). */
 fmx_status fmx_batch_create(const fmx_params *ps, int n, fmx_batch **out);
 
-/* Device bytes the batch needs for its tile descriptors and work list. */
+/* Device bytes the batch needs for its tile descriptors and work list (0
+ * for a NULL handle). */
 size_t fmx_batch_workspace_bytes(const fmx_batch *b);
 
 /* Lends the batch the buffers of its n grids (bufs[i] as in fmx_bind, set 0
@@ -353,8 +356,10 @@ fmx_status fmx_batch_set_rows(fmx_batch *b, int rows);
 
 /* Autotuner: times each candidate row extent (automatic, 1024, 512, 256, 128,
  * 64, 32) over `trial_steps` graph-replayed steps with CUDA events, keeps
- * the fastest and returns it in *chosen (0 = automatic).  The trial steps
- * advance the grids' state: set the fields afterwards. */
+ * the fastest and returns it in *chosen (0 = automatic; chosen may be NULL).
+ * The trial steps advance the grids' state: set the fields afterwards.
+ * Errors: FMX_EINVAL (trial_steps < 2), FMX_ESTATE (not bound), FMX_ECUDA,
+ * and those of fmx_batch_set_rows. */
 fmx_status fmx_batch_tune(fmx_batch *b, int trial_steps, int *chosen);
 
 /* Enqueues nsteps steps of every grid (graph replays plus at most one
@@ -366,6 +371,8 @@ fmx_status fmx_batch_step(fmx_batch *b, int nsteps);
 int fmx_batch_items(const fmx_batch *b);
 int64_t fmx_batch_launch_count(const fmx_batch *b);
 
+/* Releases the batch handle and its captured graphs (the borrowed buffers are
+ * untouched). */
 void fmx_batch_destroy(fmx_batch *b);
 
 /* Per-kernel timing of the fused engine: while enabled, every kernel of
