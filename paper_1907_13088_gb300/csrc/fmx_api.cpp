@@ -395,7 +395,9 @@ fmx_status staged_step(fmx_grid *g) {
     const int jpasses = (have_j && g->p.filter_target == FMX_FILTER_CURRENT) ? g->p.filter_passes : 0;
     // 3D, Algorithm 1 with fixed m, at most one filter pass on the current: the
     // z-marching kernels (source with the filter fused, sweeps from a plane ring)
-    const bool march = mode == FMX_ITER_FIXED && fmx::march3d_supported(g->p.dims, jpasses);
+    // (their offsets within a plane are 32-bit: larger planes take the staged kernels)
+    const bool march = mode == FMX_ITER_FIXED && fmx::march3d_supported(g->p.dims, jpasses) &&
+                       (int64_t)g->geo.ny * g->geo.pitch < ((int64_t)1 << 31);
     const T *jsrc[3];
     fmx_status s = FMX_OK;
     if (march) {
