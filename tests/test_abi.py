@@ -24,7 +24,8 @@ def fmx():
 def _declared():
     names = []
     for h in os.listdir(os.path.join(ROOT, "include")):
-        txt = open(os.path.join(ROOT, "include", h)).read()
+        with open(os.path.join(ROOT, "include", h)) as f:
+            txt = f.read()
         txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
         names += re.findall(r"\b(fmx_[a-z0-9_]+)\s*\(", txt)
     return sorted(set(names))

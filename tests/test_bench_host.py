@@ -32,7 +32,8 @@ def _commands():
     for name in sorted(os.listdir(pdir)):
         if not name.endswith(".md"):
             continue
-        lines = open(os.path.join(pdir, name)).read().splitlines()
+        with open(os.path.join(pdir, name)) as f:
+            lines = f.read().splitlines()
         buf = ""
         for line in lines:
             t = line.strip()
