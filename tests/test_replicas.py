@@ -37,7 +37,7 @@ def _rank(rank, world, port, out):
 
 def test_max_over_ranks_and_whole_job_rate_two_gloo_ranks():
     world = 2
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()  # no fork of this multi-threaded process
     mp.spawn(_rank, args=(world, _free_port(), out), nprocs=world, join=True)
     for r in range(world):
         t, rate = out[r]
