@@ -455,10 +455,13 @@ fmx_status fmx_nci_resonance(const fmx_nci_params *p, double *kx, double *ky, do
  * vacuum), and allocates nothing: its intermediates live in one file-scope
  * device array of FMX_STATIC_SCRATCH_BYTES that every GPU loading the library
  * holds until the process exits.
- *   Limit: the grid's staged workspace (fmx_workspace_bytes with the staged
- *   engine, about 13 field arrays) must fit in that array -- roughly 40 000
- *   cells in FP64 or 80 000 in FP32; larger grids return FMX_EINVAL with a
- *   message naming both sizes.
+ *   Limit: exactly the grids for which fmx_workspace_bytes(p) with
+ *   p->engine = FMX_ENGINE_STAGED is at most FMX_STATIC_SCRATCH_BYTES (13
+ *   field arrays padded to the pitch and to 256 bytes, plus the reduction
+ *   partials and status words: a little under 40 000 cells in FP64 or 80 000
+ *   in FP32); larger grids return FMX_EINVAL with a message naming both sizes.
+ *   The array lives on the current device, so the fields (and p->stream) must
+ *   be on it too: E[0] on another device returns FMX_EINVAL.
  *   The first call on a device resolves the array's device address (with
  *   that device current); make that first call before any stream capture.
  *   Every call on a device shares the same array and it keeps the last call's

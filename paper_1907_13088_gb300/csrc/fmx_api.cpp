@@ -723,6 +723,18 @@ fmx_status adjoint_impl(fmx_grid *g, void *const *Eb_, void *const *Bb_, void *c
     return check_launch(g, "adjoint launch");
 }
 
+// Chebyshev modes: the interval of A's eigenvalues and the recurrence's
+// constants, from the coefficients already in g->co (the other modes leave
+// them unused).
+void set_cheb_constants(fmx_grid *g) {
+    if (g->p.iter_mode != FMX_ITER_CHEB_FIXED && g->p.iter_mode != FMX_ITER_CHEB_RESIDUAL) return;
+    cheb_interval(g->p.dims, g->co, &g->cheb_lo, &g->cheb_hi);
+    const double al = 1.0 - g->cheb_hi, be = 1.0 - g->cheb_lo;
+    g->cheb.theta = 0.5 * (be + al);
+    g->cheb.delta = 0.5 * (be - al);
+    g->cheb.sig = g->cheb.theta / g->cheb.delta;
+}
+
 }  // namespace
 
 extern "C" {
@@ -738,13 +750,7 @@ fmx_status fmx_create(const fmx_params *p, fmx_grid **out, int *warnings) {
     g->p = *p;
     g->dt = dt;
     coefficients(p, dt, g->co);
-    if (p->iter_mode == FMX_ITER_CHEB_FIXED || p->iter_mode == FMX_ITER_CHEB_RESIDUAL) {
-        cheb_interval(p->dims, g->co, &g->cheb_lo, &g->cheb_hi);
-        const double al = 1.0 - g->cheb_hi, be = 1.0 - g->cheb_lo;
-        g->cheb.theta = 0.5 * (be + al);
-        g->cheb.delta = 0.5 * (be - al);
-        g->cheb.sig = g->cheb.theta / g->cheb.delta;
-    }
+    set_cheb_constants(g);
     g->engine = resolve_engine(p);
     g->geo = geo_of(p);
     g->elem = elem_size(p->precision);
@@ -1320,6 +1326,7 @@ fmx_status staged_steps_on(const fmx_params *p, void *const E[3], void *const B[
     g.p = q;
     g.dt = dt;
     coefficients(&q, dt, g.co);
+    set_cheb_constants(&g);
     g.engine = FMX_ENGINE_STAGED;
     g.geo = geo_of(&q);
     g.elem = elem_size(q.precision);

@@ -78,5 +78,24 @@ extern "C" fmx_status fmx_step_static(const fmx_params *p, void *const *E, void 
     void *scratch = nullptr;
     fmx_status s = scratch_address(&scratch);
     if (s != FMX_OK) return s;
+    // The scratch belongs to the current device: the fields must live there too.
+    int dev = -1;
+    cudaPointerAttributes a;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaPointerGetAttributes(&a, E[0]) != cudaSuccess) {
+        cudaGetLastError();
+        fmx::set_last_error("fmx_step_static: E[0] is not a pointer the CUDA runtime knows");
+        return FMX_EINVAL;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) {
+        fmx::set_last_error("fmx_step_static: E[0] is not device memory");
+        return FMX_EINVAL;
+    }
+    if (a.device != dev) {
+        char msg[160];
+        snprintf(msg, sizeof(msg), "fmx_step_static: the fields are on device %d but device %d is current", a.device,
+                 dev);
+        fmx::set_last_error(msg);
+        return FMX_EINVAL;
+    }
     return fmx::staged_steps_on(p, E, B, J, scratch, FMX_STATIC_SCRATCH_BYTES, nsteps);
 }
