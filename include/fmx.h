@@ -73,7 +73,7 @@ enum { FMX_F32 = 0, FMX_F64 = 1 };                        /* storage and sweep p
  * the staged engine. */
 enum { FMX_ITER_FIXED = 0, FMX_ITER_RESIDUAL = 1, FMX_ITER_CHEB_FIXED = 2, FMX_ITER_CHEB_RESIDUAL = 3 };
 enum { FMX_FILTER_NONE = 0, FMX_FILTER_CURRENT = 1, FMX_FILTER_FIELDS = 2 };
-enum { FMX_ENGINE_AUTO = 0, FMX_ENGINE_STAGED = 1, FMX_ENGINE_FUSED = 2 };
+enum { FMX_ENGINE_AUTO = 0, FMX_ENGINE_STAGED = 1, FMX_ENGINE_FUSED = 2, FMX_ENGINE_RESIDENT = 3 };
 enum { FMX_HOST = 0, FMX_DEVICE = 1 };                    /* where a copy source/target lives */
 
 /* component bits (index order of the pointer arrays below) */

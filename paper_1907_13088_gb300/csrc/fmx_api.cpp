@@ -58,12 +58,35 @@ int64_t pitch_of(const fmx_params *p) {
     return (p->n[0] + q - 1) / q * q;
 }
 
+// Cells per grid of the resident engine (one cluster of 8-16 SMs runs the
+// whole step, so the grid must be small), and the sizes up to which the
+// automatic choice prefers it for residual-controlled solves (beyond them
+// the staged kernels on every SM win: FP64 arithmetic runs at 1/64 of the
+// FP32 rate on this part, so the FP64 limit is lower).
+constexpr int64_t kResidentMaxCells = (int64_t)1 << 18;
+constexpr int64_t kResidentAutoCells64 = (int64_t)1 << 14;
+constexpr int64_t kResidentAutoCells32 = (int64_t)1 << 16;
+
+bool resident_supported(const fmx_params *p) {
+    const int64_t cells = p->n[0] * p->n[1] * p->n[2];
+    if (cells > kResidentMaxCells) return false;
+    if (p->iter_mode != FMX_ITER_FIXED && p->iter_mode != FMX_ITER_RESIDUAL) return false;
+    if (p->filter_target == FMX_FILTER_FIELDS && p->filter_passes > 0) return false;
+    return true;
+}
+
 // Which engine runs a step of this problem.
 int resolve_engine(const fmx_params *p) {
     const bool fusable = fmx::fused2d_supported(p);
     if (p->engine == FMX_ENGINE_FUSED) return fusable ? FMX_ENGINE_FUSED : -1;
     if (p->engine == FMX_ENGINE_STAGED) return FMX_ENGINE_STAGED;
-    return fusable ? FMX_ENGINE_FUSED : FMX_ENGINE_STAGED;
+    const bool resident = resident_supported(p);
+    if (p->engine == FMX_ENGINE_RESIDENT) return resident ? FMX_ENGINE_RESIDENT : -1;
+    if (fusable) return FMX_ENGINE_FUSED;
+    const int64_t cells = p->n[0] * p->n[1] * p->n[2];
+    const int64_t lim = p->precision == FMX_F64 ? kResidentAutoCells64 : kResidentAutoCells32;
+    if (resident && p->iter_mode == FMX_ITER_RESIDUAL && cells <= lim) return FMX_ENGINE_RESIDENT;
+    return FMX_ENGINE_STAGED;
 }
 
 // Eigenvalues of a real symmetric 3x3 matrix by cyclic Jacobi rotations:
@@ -156,7 +179,7 @@ fmx_status validate(const fmx_params *p, double *dt_out, int *warn) {
     if (p->filter_passes < 0 || p->filter_passes > 1024) return fail(FMX_EINVAL, "filter_passes out of range");
     if (p->filter_target < FMX_FILTER_NONE || p->filter_target > FMX_FILTER_FIELDS)
         return fail(FMX_EINVAL, "bad filter_target");
-    if (p->engine < FMX_ENGINE_AUTO || p->engine > FMX_ENGINE_FUSED) return fail(FMX_EINVAL, "bad engine");
+    if (p->engine < FMX_ENGINE_AUTO || p->engine > FMX_ENGINE_RESIDENT) return fail(FMX_EINVAL, "bad engine");
     const int64_t q = (int64_t)(16 / elem_size(p->precision));
     if (p->pitch != 0 && (p->pitch < p->n[0] || p->pitch % q != 0))
         return fail(FMX_EINVAL, "pitch must be >= n[0] and a multiple of 16 bytes");
@@ -174,7 +197,9 @@ fmx_status validate(const fmx_params *p, double *dt_out, int *warn) {
         for (int a = 1; a < 3; ++a) dmin = p->d[a] < dmin ? p->d[a] : dmin;
         if (p->c * dt > dmin / sqrt(2.0)) w |= FMX_WARN_ANORM;  // App. C bound, 3D
     }
-    if (resolve_engine(p) < 0) return fail(FMX_EUNSUPPORTED, "the fused engine does not cover this problem");
+    if (resolve_engine(p) < 0)
+        return fail(FMX_EUNSUPPORTED, "the %s engine does not cover this problem",
+                    p->engine == FMX_ENGINE_FUSED ? "fused" : "resident");
     *dt_out = dt;
     if (warn) *warn = w;
     return FMX_OK;
@@ -283,7 +308,7 @@ struct fmx_grid {
 
 namespace {
 
-int staged_arrays(int engine) { return engine == FMX_ENGINE_STAGED ? 13 : 1; }
+int staged_arrays(int engine) { return engine == FMX_ENGINE_FUSED ? 1 : 13; }
 
 fmx::Geo geo_of(const fmx_params *p) {
     fmx::Geo g;
@@ -490,6 +515,45 @@ fmx_status staged_step(fmx_grid *g) {
             if ((s = filter_in_place<T>(g, P.B[q], g->p.filter_passes)) != FMX_OK) return s;
         }
     }
+    return FMX_OK;
+}
+
+// Resident engine: nsteps steps in one cluster launch.  Residual mode reads
+// the solver status back once (synchronising: it reports FMX_ENOCONV and the
+// sweep counts); fixed m stays asynchronous.
+template <typename T>
+fmx_status resident_steps(fmx_grid *g, int nsteps) {
+    if (nsteps == 0) return FMX_OK;
+    const fmx::Coef<T> c = make_coef<T>(g->co);
+    const fmx::StagedPtrs<T> P = staged_ptrs<T>(g);
+    const bool resid = g->p.iter_mode == FMX_ITER_RESIDUAL;
+    const bool have_j = g->buf.J[0] != nullptr;
+    const int jpasses = (have_j && g->p.filter_target == FMX_FILTER_CURRENT) ? g->p.filter_passes : 0;
+    const int n = fmx::launch_resident<T>(g->geo, g->p.dims, c, P, nsteps, resid, g->p.m, g->p.tol * g->p.tol,
+                                          g->p.m_max, jpasses, g->stream);
+    if (n < 0) return cuda_fail(cudaGetLastError(), "resident launch");
+    g->launches += n;
+    fmx_status s = check_launch(g, "resident launch");
+    if (s != FMX_OK) return s;
+    if (!resid) {
+        g->last_sweeps = g->p.m;
+        g->total_sweeps += (int64_t)g->p.m * nsteps;
+        g->steps += nsteps;
+        return FMX_OK;
+    }
+    fmx::DevStatus hs;
+    cudaError_t e = cudaMemcpyAsync(&hs, g->st, sizeof(hs), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "resident status read-back");
+    g->last_sweeps = hs.count;
+    g->total_sweeps += hs.sweeps_total;
+    g->last_resid = hs.nrm2 > 0.0 ? sqrt(hs.r2 / hs.nrm2) : 0.0;
+    if (hs.noconv) {
+        // as the staged engine: the failing step is applied but not counted
+        g->steps += hs.steps - 1;
+        return fail(FMX_ENOCONV, "residual %.3g above tol after %d sweeps", g->last_resid, hs.count);
+    }
+    g->steps += nsteps;
     return FMX_OK;
 }
 
@@ -794,7 +858,7 @@ fmx_status fmx_bind(fmx_grid *g, const fmx_buffers *b) {
     g->buf = *b;
     char *w = (char *)b->work;
     const size_t fb = align_up(g->field_bytes, kAlign);
-    if (g->engine == FMX_ENGINE_STAGED) {
+    if (g->engine != FMX_ENGINE_FUSED) {
         for (int c = 0; c < 3; ++c) { g->jf[c] = w; w += fb; }
         g->tmp = w; w += fb;
         for (int c = 0; c < 3; ++c) { g->dEp[c] = w; w += fb; }
@@ -878,6 +942,11 @@ fmx_status fmx_step(fmx_grid *g, int nsteps) {
     if (nsteps < 0) return fail(FMX_EINVAL, "nsteps < 0");
     if (g->engine == FMX_ENGINE_FUSED) {
         return g->p.precision == FMX_F64 ? fused_step<double>(g, nsteps) : fused_step<float>(g, nsteps);
+    }
+    // the resident launch applies one current factor to all its steps: a time
+    // profile still being consumed takes the staged kernels
+    if (g->engine == FMX_ENGINE_RESIDENT && g->jprof_pos >= g->jprof.size()) {
+        return g->p.precision == FMX_F64 ? resident_steps<double>(g, nsteps) : resident_steps<float>(g, nsteps);
     }
     for (int n = 0; n < nsteps; ++n) {
         fmx_status s = g->p.precision == FMX_F64 ? staged_step<double>(g) : staged_step<float>(g);

@@ -36,6 +36,8 @@ struct DevStatus {
     int noconv;      // 1 when it stopped at m_max
     int err;         // latched device error (FMX_ETIMEOUT, ...)
     double cheb_rho; // Chebyshev mode: rho of the last sweep
+    int steps;       // resident engine: steps completed by the last launch
+    long long sweeps_total;  // resident engine: sweeps of all those steps
 };
 
 // Chebyshev acceleration: M = 1 - A has its spectrum in [1 - hi, 1 - lo];
@@ -111,6 +113,20 @@ int launch_march3d_sweep(const Geo &g, const Coef<T> &c, const T *const dEp[3], 
 // that path does not apply
 template <typename T>
 int launch_march3d_faraday(const Geo &g, const Coef<T> &c, const T *const E[3], T *const B[3], cudaStream_t s);
+
+// Resident engine (resident.cu): nsteps whole steps in one launch of one
+// thread-block cluster (grids small enough to stay in L2).  Algorithm 1 with
+// m sweeps, or to the residual stop when resid; jpasses binomial passes on the
+// current (once per launch, into P.jf).  Results in P.st (count = sweeps of
+// the last step, steps, sweeps_total, noconv).  Returns 1, or -1 when the
+// launch failed.
+template <typename T>
+int launch_resident(const Geo &g, int dims, const Coef<T> &c, const StagedPtrs<T> &P, int nsteps, bool resid, int m,
+                    double tol2, int m_max, int jpasses, cudaStream_t s);
+// CTAs in the cluster the resident kernel launches with (16 where the device
+// runs clusters of 16, else 8)
+template <typename T>
+int resident_cluster_size(int dims);
 
 // Diagnostics (diag.cu): writes 6 FP64 values to out_dev (w_scheme sum,
 // w_plain sum, divb max, divb sum sq, gauss max, gauss sum sq).

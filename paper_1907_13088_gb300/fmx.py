@@ -24,7 +24,7 @@ FMX_OK, FMX_EINVAL, FMX_ECFL, FMX_ENOCONV, FMX_ECUDA, FMX_ETIMEOUT, FMX_ESTATE, 
 FMX_F32, FMX_F64 = 0, 1
 FMX_ITER_FIXED, FMX_ITER_RESIDUAL, FMX_ITER_CHEB_FIXED, FMX_ITER_CHEB_RESIDUAL = 0, 1, 2, 3
 FMX_FILTER_NONE, FMX_FILTER_CURRENT, FMX_FILTER_FIELDS = 0, 1, 2
-FMX_ENGINE_AUTO, FMX_ENGINE_STAGED, FMX_ENGINE_FUSED = 0, 1, 2
+FMX_ENGINE_AUTO, FMX_ENGINE_STAGED, FMX_ENGINE_FUSED, FMX_ENGINE_RESIDENT = 0, 1, 2, 3
 FMX_HOST, FMX_DEVICE = 0, 1
 FMX_EX, FMX_EY, FMX_EZ, FMX_BX, FMX_BY, FMX_BZ, FMX_JX, FMX_JY, FMX_JZ = (1 << i for i in range(9))
 FMX_E, FMX_B, FMX_J = 7, 7 << 3, 7 << 6

@@ -91,6 +91,15 @@ def test_validation_codes(fmx):
         fmx.FMX_EUNSUPPORTED
     assert fmx.create_status(fmx.make_params((16, 16), engine=fmx.FMX_ENGINE_FUSED, m=4, filter_passes=3))[0] == \
         fmx.FMX_OK
+    # the resident engine: small grids, Algorithm 1 (fixed m or residual), no field filter
+    R = fmx.FMX_ENGINE_RESIDENT
+    assert fmx.create_status(fmx.make_params((64, 64), iter_mode=1, precision=1, engine=R))[0] == fmx.FMX_OK
+    assert fmx.create_status(fmx.make_params((16, 16, 16), m=4, engine=R))[0] == fmx.FMX_OK
+    assert fmx.create_status(fmx.make_params((1024, 1024), iter_mode=1, engine=R))[0] == fmx.FMX_EUNSUPPORTED
+    assert fmx.create_status(fmx.make_params((64, 64), iter_mode=3, engine=R))[0] == fmx.FMX_EUNSUPPORTED
+    assert fmx.create_status(fmx.make_params((64, 64), filter_passes=1, filter_target=fmx.FMX_FILTER_FIELDS,
+                                             engine=R))[0] == fmx.FMX_EUNSUPPORTED
+    assert fmx.create_status(fmx.make_params((16, 16), engine=4))[0] == fmx.FMX_EINVAL
     assert b"CFL" in fmx.fmx_strerror(fmx.FMX_ECFL)
 
 
@@ -107,6 +116,9 @@ def test_sizes(fmx):
     fb = fmx.fmx_field_bytes(ctypes.byref(staged))
     assert fmx.fmx_workspace_bytes(ctypes.byref(staged)) >= 13 * fb
     assert fmx.fmx_workspace_bytes(ctypes.byref(fused)) < 2 * fb
+    res = fmx.make_params((100, 100), iter_mode=1, engine=fmx.FMX_ENGINE_RESIDENT)
+    sta = fmx.make_params((100, 100), iter_mode=1, engine=fmx.FMX_ENGINE_STAGED)
+    assert fmx.fmx_workspace_bytes(ctypes.byref(res)) == fmx.fmx_workspace_bytes(ctypes.byref(sta))
     bad = fmx.make_params((16, 16), courant=2.0)
     assert fmx.fmx_workspace_bytes(ctypes.byref(bad)) == 0
 
