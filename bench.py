@@ -492,6 +492,86 @@ def run_3d(args):
     print(json.dumps(line), flush=True)
 
 
+# FP64 arithmetic of one 2D cell-step of the fused FP64 kernel as executed
+# (halo and warm-up rows included): (DADD + DMUL + 2 x DFMA) thread
+# instructions of one launch over its output cells, from the ncu capture of
+# k_fused2d<double, 4, 3> at 2048^2 (profiles/k_fused2d_f64_2048.md):
+# (562.4 M + 17.4 M + 2 x 463.8 M) / 2048^2 = 359
+FP64_FLOPS_PER_CELL_STEP_2D = 359
+
+
+def run_f64(args):
+    """The 2D benchmark recipe in FP64: 4096^2, power-law spectrum up to
+    k_max = N/8, static solenoidal current (width 16) re-filtered by 3
+    binomial passes every step, m = 4, dt = 0.5 dt_CFL, on the fused engine
+    (one launch per step, all six components).  Two rooflines: HBM (15
+    values of 8 bytes per cell-step) and FP64 arithmetic against the FMA rate
+    measured in this run (fmx_fma_peak)."""
+    import numpy as np
+    import torch
+    from paper_1907_13088_gb300 import build, synth
+    build.build()
+    from paper_1907_13088_gb300 import fmx
+    n = args.n2d
+    E, B = synth.power_law_fields((n, n), n // 8, SEED, dtype=np.float64)
+    J = synth.solenoidal_current((n, n), SEED + 1, width=16.0, rms=1e-3, dtype=np.float64)
+    g = fmx.Grid((n, n), precision=fmx.FMX_F64, m=M_SWEEPS, filter_passes=PASSES, courant=COURANT,
+                 engine=fmx.FMX_ENGINE_FUSED)
+    g.set_fields(E, B)
+    g.set_current(J)
+    del E, B, J
+    g.step(args.warmup)
+    torch.cuda.synchronize()
+    fp64_peak = fmx.fma_peak(fmx.FMX_F64, g.stream)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    l0 = g.launches
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    t0 = time.time()
+    ev0.record(g.stream)
+    g.step(args.steps)
+    ev1.record(g.stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    ms = ev0.elapsed_time(ev1)
+    clocks = sampler.summary(t0, t1)
+    sampler.stop()
+    launches = g.launches - l0
+    prof_steps = max(20, min(100, args.steps))
+    g.profile(True)
+    g.step(prof_steps)
+    ks = g.profile_read()
+    g.profile(False)
+    cells = n * n
+    peak, peak_src = _peaks()
+    bpc = 15 * 8
+    dom = max(ks, key=lambda k: k["total_ms"])
+    per_launch_s = dom["total_ms"] / 1e3 / dom["launches"]
+    achieved = dom["bytes_per_launch"] / per_launch_s / 1e9
+    flops = FP64_FLOPS_PER_CELL_STEP_2D * cells / per_launch_s / 1e12
+    line = {
+        "metric": METRIC, "value": round(cells * args.steps / (ms / 1e3) / 1e9, 3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"2D periodic {n}x{n} FP64, dt=0.5 dt_CFL, power-law spectrum k_max=N/8, static "
+                               "solenoidal J (width 16), 3-pass binomial current filter every step, m=4 sweeps",
+                   "engine": "fused2d (one kernel per step, k_fused2d<double>)",
+                   "l2": f"inputs larger than L2 ({15 * 8 * cells / 1e9:.2f} GB of fields per step vs 129 MB L2)"},
+        "roofline": {"bound": "alu", "achieved": round(flops, 3), "peak": round(fp64_peak / 1e12, 3),
+                     "unit": "TFLOP/s", "frac": round(flops / (fp64_peak / 1e12), 4), "traffic": None,
+                     "kernel": dom["name"], "flops_per_cell_step": FP64_FLOPS_PER_CELL_STEP_2D,
+                     "peak_source": "FP64 FMA rate measured in this run (fmx_fma_peak: independent FMA chains on "
+                                    "every SM, CUDA events)",
+                     "hbm": {"achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                             "frac": round(achieved / peak, 4), "peak_source": peak_src, "bytes_per_cell_step": bpc},
+                     "timing": f"CUDA events around each launch, {prof_steps} steps"},
+        "gpu_launches": int(launches), "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_res64(args):
     """The 64 x 64 FP64 plane-wave case: 8 TM plane waves (|n| <= 8), no
     current, no filter, the solve to a relative residual of 1e-13 every step
@@ -647,7 +727,9 @@ def _parser():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
-    ap.add_argument("--workload", choices=("2d4096", "batch256", "adjoint1024", "3d512", "res64"), default="2d4096")
+    ap.add_argument("--workload", choices=("2d4096", "batch256", "adjoint1024", "3d512", "res64", "2d4096f64"),
+                    default="2d4096")
+    ap.add_argument("--n2d", type=int, default=NX, help="grid side of the 2d4096f64 workload (profiler captures only)")
     ap.add_argument("--n3d", type=int, default=512, help="cube side of the 3d512 workload (profiler captures only)")
     return ap
 
@@ -665,6 +747,8 @@ def main():
         run_adjoint(args)
     elif args.workload == "3d512":
         run_3d(args)
+    elif args.workload == "2d4096f64":
+        run_f64(args)
     elif args.workload == "res64":
         run_res64(args)
     else:

@@ -391,6 +391,16 @@ typedef struct {
 fmx_status fmx_profile_enable(fmx_grid *g, int enable);
 fmx_status fmx_profile_read(fmx_grid *g, fmx_kernel_stat *out, int max, int *n);
 
+/* Measured fused multiply-add rate of the current device in the given
+ * precision (FMX_F32 or FMX_F64), in flops per second (2 per FMA): a launch
+ * of independent FMA chains over every SM, timed with CUDA events on
+ * `stream` (cudaStream_t; NULL: legacy stream), best of three after a
+ * warm-up; synchronising, nothing allocated.  The arithmetic-roofline
+ * denominator reported beside the HBM one (the FP64 step on this class of
+ * part is bound by FP64 arithmetic, not by HBM).  Not part of the paper.
+ * Errors: FMX_EINVAL (bad precision, NULL output), FMX_ECUDA. */
+fmx_status fmx_fma_peak(int precision, void *stream, double *flops_per_s);
+
 /* ---------------------------------------------------------------------
  * NCI closed-form tools (Sec. 3, App. E).  For a cold beam drifting along x
  * at v -> c on a 2D grid (dx, dy) with dt = courant * dt_CFL,

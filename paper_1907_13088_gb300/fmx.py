@@ -124,6 +124,7 @@ def _load():
                                             ctypes.POINTER(ctypes.c_int)]),
         "fmx_nci_resonance": (ctypes.c_int, [ctypes.POINTER(fmx_nci_params), ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+        "fmx_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -178,6 +179,7 @@ fmx_batch_launch_count = _lib.fmx_batch_launch_count
 fmx_batch_destroy = _lib.fmx_batch_destroy
 fmx_profile_read = _lib.fmx_profile_read
 fmx_nci_resonance = _lib.fmx_nci_resonance
+fmx_fma_peak = _lib.fmx_fma_peak
 FMX_STATIC_SCRATCH_BYTES = 4 << 20
 
 
@@ -547,3 +549,13 @@ def nci_resonance(device="cuda", stream=None, **kw):
                             ctypes.c_void_p(stream.cuda_stream)), "fmx_nci_resonance")
     stream.synchronize()
     return dict(kx=kx, ky=ky, gamma=gamma, best=tuple(best.tolist()), nus=list(range(-p.nu_max, p.nu_max + 1)))
+
+
+def fma_peak(precision=FMX_F32, stream=None) -> float:
+    """Measured FMA rate of the current device (flops/s) in FP32 or FP64
+    (fmx_fma_peak), on `stream` (a torch stream; default: the current one)."""
+    import torch
+    stream = stream or torch.cuda.current_stream()
+    out = ctypes.c_double(0.0)
+    check(fmx_fma_peak(int(precision), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(out)), "fmx_fma_peak")
+    return out.value

@@ -100,6 +100,11 @@ def test_validation_codes(fmx):
     assert fmx.create_status(fmx.make_params((64, 64), filter_passes=1, filter_target=fmx.FMX_FILTER_FIELDS,
                                              engine=R))[0] == fmx.FMX_EUNSUPPORTED
     assert fmx.create_status(fmx.make_params((16, 16), engine=4))[0] == fmx.FMX_EINVAL
+    # the FMA-rate measurement refuses bad arguments before any device work
+    import ctypes
+    out = ctypes.c_double(0.0)
+    assert fmx.fmx_fma_peak(7, None, ctypes.byref(out)) == fmx.FMX_EINVAL
+    assert fmx.fmx_fma_peak(fmx.FMX_F64, None, None) == fmx.FMX_EINVAL
     assert b"CFL" in fmx.fmx_strerror(fmx.FMX_ECFL)
 
 
