@@ -481,6 +481,28 @@ fmx_status fmx_nci_resonance(const fmx_nci_params *p, double *kx, double *ky, do
  *   Errors as fmx_step (FMX_EINVAL, FMX_ECFL, FMX_ENOCONV, FMX_ECUDA). */
 fmx_status fmx_step_static(const fmx_params *p, void *const *E, void *const *B, const void *const *J, int nsteps);
 
+/* Streams steps from and to host memory: for each record, the state
+ * (E, B) and optionally the current are replaced by host arrays, the grid
+ * advances one step, and E, B are copied back out -- the loop a caller runs
+ * when every step's inputs come from the host and its result goes back
+ * there (not part of the paper).
+ *   in[0..5]: E x, y, z and B x, y, z of the step (host or device arrays of
+ *             n_x * n_y * n_z values, x fastest, no padding); in[6..8]: J, or
+ *             all three NULL to keep the bound current;
+ *   out[0..5]: where E, B after the step go (NULL: not read back).
+ * Page-locked host memory lets the copies run asynchronously.  On the fused
+ * engine the upload of step i+1 and the read-back of step i run concurrently
+ * on two copy streams of the grid (created on first use), each step reading
+ * state set 0 and writing set 1; the other engines copy and step in order on
+ * the grid's stream.  Synchronising: every output is in place on return.
+ * Errors: FMX_EINVAL (NULL or partial arrays), FMX_ESTATE (not bound, or a
+ * current given with no J bound), the errors of fmx_step, FMX_ECUDA. */
+typedef struct {
+    const void *in[9];
+    void *out[6];
+} fmx_host_step;
+fmx_status fmx_step_host(fmx_grid *g, const fmx_host_step *io, int count);
+
 /* Releases the handle (host memory only; borrowed buffers are untouched). */
 void fmx_destroy(fmx_grid *g);
 

@@ -288,6 +288,10 @@ struct fmx_grid {
     // and join events (created on first use)
     cudaStream_t s_tm = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // fmx_step_host: copy-in and copy-out streams and their events (created on
+    // first use)
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_comp = nullptr, ev_out = nullptr;
     // Chebyshev modes: the interval holding the eigenvalues of A, and the
     // recurrence's constants
     double cheb_lo = 0.0, cheb_hi = 0.0;
@@ -653,13 +657,22 @@ fmx_status fused_step(fmx_grid *g, int nsteps, StepPre pre = nullptr) {
     return check_launch(g, "fused step launch");
 }
 
-fmx_status copy_rows(fmx_grid *g, void *dst, size_t dpitch, const void *src, size_t spitch, bool sync) {
+// One component between a dense host or device array (rows of n_x values)
+// and the grid's pitched array: one 1D copy when the rows are contiguous on
+// both sides, else a 2D copy; on `stream` (the grid's stream by default).
+fmx_status copy_rows(fmx_grid *g, void *dst, size_t dpitch, const void *src, size_t spitch, bool sync,
+                     cudaStream_t stream = nullptr) {
+    const cudaStream_t st = stream ? stream : g->stream;
     const size_t width = (size_t)g->geo.nx * g->elem;
     const size_t rows = (size_t)g->geo.ny * (size_t)g->geo.nz;
-    cudaError_t e = cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, rows, cudaMemcpyDefault, g->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2DAsync");
+    cudaError_t e;
+    if (dpitch == width && spitch == width)
+        e = cudaMemcpyAsync(dst, src, width * rows, cudaMemcpyDefault, st);
+    else
+        e = cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, rows, cudaMemcpyDefault, st);
+    if (e != cudaSuccess) return cuda_fail(e, "copy of a component");
     if (sync) {
-        e = cudaStreamSynchronize(g->stream);
+        e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     }
     return FMX_OK;
@@ -1339,12 +1352,95 @@ fmx_status fmx_profile_read(fmx_grid *g, fmx_kernel_stat *out, int max, int *n) 
     return FMX_OK;
 }
 
+fmx_status fmx_step_host(fmx_grid *g, const fmx_host_step *io, int count) {
+    if (!g || (!io && count > 0)) return fail(FMX_EINVAL, "NULL argument");
+    if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
+    if (count < 0) return fail(FMX_EINVAL, "count < 0");
+    for (int i = 0; i < count; ++i) {
+        for (int c = 0; c < 6; ++c)
+            if (!io[i].in[c]) return fail(FMX_EINVAL, "step %d: in[%d] is NULL", i, c);
+        const bool any_j = io[i].in[6] || io[i].in[7] || io[i].in[8];
+        if (any_j && !(io[i].in[6] && io[i].in[7] && io[i].in[8]))
+            return fail(FMX_EINVAL, "step %d: give all three current components or none", i);
+        if (any_j && !g->buf.J[0]) return fail(FMX_ESTATE, "step %d: a current is given but no J buffers are bound", i);
+    }
+    const size_t sp = (size_t)g->geo.nx * g->elem, dp = (size_t)g->geo.pitch * g->elem;
+    auto dst_in = [&](int set, int c) -> void * {
+        return c < 3 ? g->buf.E[set][c] : (c < 6 ? g->buf.B[set][c - 3] : g->buf.J[c - 6]);
+    };
+    auto step1 = [&]() {
+        return g->p.precision == FMX_F64 ? (g->engine == FMX_ENGINE_FUSED ? fused_step<double>(g, 1)
+                                                                          : fmx_step(g, 1))
+                                         : (g->engine == FMX_ENGINE_FUSED ? fused_step<float>(g, 1) : fmx_step(g, 1));
+    };
+    if (g->engine != FMX_ENGINE_FUSED) {
+        // in-place engines: upload, step and read back in order on the grid's stream
+        for (int i = 0; i < count; ++i) {
+            fmx_status s = FMX_OK;
+            for (int c = 0; c < 9 && s == FMX_OK; ++c)
+                if (io[i].in[c]) s = copy_rows(g, dst_in(g->cur, c), dp, io[i].in[c], sp, false);
+            if (s == FMX_OK) s = step1();
+            for (int c = 0; c < 6 && s == FMX_OK; ++c)
+                if (io[i].out[c]) s = copy_rows(g, io[i].out[c], sp, dst_in(g->cur, c), dp, false);
+            if (s != FMX_OK) return s;
+        }
+        cudaError_t e = cudaStreamSynchronize(g->stream);
+        return e == cudaSuccess ? FMX_OK : cuda_fail(e, "cudaStreamSynchronize");
+    }
+    // fused engine: every step reads state set 0 and writes set 1, so the
+    // upload of step i+1 (into set 0, on the copy-in stream, after step i has
+    // read it) overlaps the read-back of step i (from set 1, on the copy-out
+    // stream); step i+1 waits for both
+    cudaError_t e = cudaSuccess;
+    if (!g->s_in) e = cudaStreamCreateWithFlags(&g->s_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !g->s_out) e = cudaStreamCreateWithFlags(&g->s_out, cudaStreamNonBlocking);
+    for (cudaEvent_t *ev : {&g->ev_in, &g->ev_comp, &g->ev_out})
+        if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    // the copies start after whatever the grid's stream already holds
+    if (e == cudaSuccess) e = cudaEventRecord(g->ev_comp, g->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(g->ev_out, g->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "host-streaming set-up");
+    for (int i = 0; i < count; ++i) {
+        e = cudaStreamWaitEvent(g->s_in, g->ev_comp, 0);  // step i-1 has read set 0 and J
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+        for (int c = 0; c < 9; ++c) {
+            if (!io[i].in[c]) continue;
+            fmx_status s = copy_rows(g, dst_in(0, c), dp, io[i].in[c], sp, false, g->s_in);
+            if (s != FMX_OK) return s;
+        }
+        e = cudaEventRecord(g->ev_in, g->s_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(g->stream, g->ev_in, 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(g->stream, g->ev_out, 0);  // step i-1's read-back of set 1
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+        g->cur = 0;
+        fmx_status s = step1();
+        if (s != FMX_OK) return s;
+        e = cudaEventRecord(g->ev_comp, g->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(g->s_out, g->ev_comp, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+        for (int c = 0; c < 6; ++c) {
+            if (!io[i].out[c]) continue;
+            s = copy_rows(g, io[i].out[c], sp, dst_in(1, c), dp, false, g->s_out);
+            if (s != FMX_OK) return s;
+        }
+        e = cudaEventRecord(g->ev_out, g->s_out);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    }
+    // later work on the grid's stream follows the last read-back
+    e = cudaStreamWaitEvent(g->stream, g->ev_out, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->s_out);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    return e == cudaSuccess ? FMX_OK : cuda_fail(e, "host-streaming synchronise");
+}
+
 void fmx_destroy(fmx_grid *g) {
     if (!g) return;
     for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
-    if (g->ev_fork) cudaEventDestroy(g->ev_fork);
-    if (g->ev_join) cudaEventDestroy(g->ev_join);
-    if (g->s_tm) cudaStreamDestroy(g->s_tm);  // its work was joined into the grid's stream
+    for (cudaEvent_t e : {g->ev_fork, g->ev_join, g->ev_in, g->ev_comp, g->ev_out})
+        if (e) cudaEventDestroy(e);
+    // their work was joined into the grid's stream or synchronised
+    for (cudaStream_t s : {g->s_tm, g->s_in, g->s_out})
+        if (s) cudaStreamDestroy(s);
     delete g;
 }
 

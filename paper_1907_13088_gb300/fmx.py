@@ -51,6 +51,10 @@ class fmx_kernel_stat(ctypes.Structure):
                 ("bytes_per_launch", ctypes.c_double)]
 
 
+class fmx_host_step(ctypes.Structure):
+    _fields_ = [("inp", ctypes.c_void_p * 9), ("out", ctypes.c_void_p * 6)]
+
+
 class fmx_nci_params(ctypes.Structure):
     _fields_ = [("dx", ctypes.c_double), ("dy", ctypes.c_double), ("c", ctypes.c_double),
                 ("courant", ctypes.c_double), ("omega_p", ctypes.c_double), ("shape_order", ctypes.c_int),
@@ -125,6 +129,7 @@ def _load():
         "fmx_nci_resonance": (ctypes.c_int, [ctypes.POINTER(fmx_nci_params), ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
         "fmx_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+        "fmx_step_host": (ctypes.c_int, [G, ctypes.POINTER(fmx_host_step), ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -180,6 +185,7 @@ fmx_batch_destroy = _lib.fmx_batch_destroy
 fmx_profile_read = _lib.fmx_profile_read
 fmx_nci_resonance = _lib.fmx_nci_resonance
 fmx_fma_peak = _lib.fmx_fma_peak
+fmx_step_host = _lib.fmx_step_host
 FMX_STATIC_SCRATCH_BYTES = 4 << 20
 
 
@@ -345,6 +351,22 @@ class Grid:
     # -- work ------------------------------------------------------------
     def step(self, nsteps=1):
         check(fmx_step(self.handle, int(nsteps)), "fmx_step")
+
+    def step_host(self, steps):
+        """fmx_step_host: ``steps`` is a list of (inputs, outputs), inputs a
+        (9 or 6, nz, ny, nx) host array (E, B and optionally J; pinned memory
+        lets the copies overlap), outputs a (6, nz, ny, nx) host array or
+        None.  One step per entry; returns when every output is written."""
+        recs = (fmx_host_step * len(steps))()
+        keep = []
+        for i, (inp, out) in enumerate(steps):
+            for c in range(9):
+                recs[i].inp[c] = inp[c].ctypes.data if c < len(inp) else None
+            for c in range(6):
+                recs[i].out[c] = out[c].ctypes.data if out is not None else None
+            keep.append((inp, out))
+        check(fmx_step_host(self.handle, recs, len(steps)), "fmx_step_host")
+        del keep
 
     def filter(self, mask, passes):
         check(fmx_filter(self.handle, int(mask), int(passes)), "fmx_filter")
