@@ -481,6 +481,18 @@ fmx_status fmx_nci_resonance(const fmx_nci_params *p, double *kx, double *ky, do
  *   Errors as fmx_step (FMX_EINVAL, FMX_ECFL, FMX_ENOCONV, FMX_ECUDA). */
 fmx_status fmx_step_static(const fmx_params *p, void *const *E, void *const *B, const void *const *J, int nsteps);
 
+/* Per-grid options of the kernels (not part of the paper):
+ *   FMX_OPT_SWEEPS_PER_PASS: sweeps of Algorithm 1 per z-march pass of the
+ *     3D FP32 kernels, 1 (one pass per sweep) or 2 (temporal blocking: pairs
+ *     of sweeps in one pass, the intermediate sweep kept on chip on a tile
+ *     grown by one cell; an odd last sweep takes a pass of its own).  Same
+ *     results to FP32 rounding.  Default 1.
+ * fmx_set_option returns FMX_EINVAL for an unknown option or value;
+ * fmx_get_option returns the value, or -1 (unknown option or NULL grid). */
+enum { FMX_OPT_SWEEPS_PER_PASS = 1 };
+fmx_status fmx_set_option(fmx_grid *g, int option, int value);
+int fmx_get_option(const fmx_grid *g, int option);
+
 /* Streams steps from and to host memory: for each record, the state
  * (E, B) and optionally the current are replaced by host arrays, the grid
  * advances one step, and E, B are copied back out -- the loop a caller runs

@@ -292,6 +292,8 @@ struct fmx_grid {
     // first use)
     cudaStream_t s_in = nullptr, s_out = nullptr;
     cudaEvent_t ev_in = nullptr, ev_comp = nullptr, ev_out = nullptr;
+    // sweeps of Algorithm 1 per z-march pass of the 3D kernels (fmx_set_option)
+    int sweeps_per_pass = 1;
     // Chebyshev modes: the interval holding the eigenvalues of A, and the
     // recurrence's constants
     double cheb_lo = 0.0, cheb_hi = 0.0;
@@ -444,6 +446,24 @@ fmx_status staged_step(fmx_grid *g) {
         const T *dp[3] = {P.dEp[0], P.dEp[1], P.dEp[2]};
         bool updated = false;
         for (int it = 0; it < g->p.m; ++it) {
+            // two sweeps per z-march pass (temporal blocking) where the grid asks
+            // for it; the pass that ends the solve also applies the update
+            if (march && g->sweeps_per_pass == 2 && it + 2 <= g->p.m) {
+                const bool last = it + 2 == g->p.m;
+                T *out[3];
+                for (int q = 0; q < 3; ++q) out[q] = last ? P.E[q] : (in[0] == P.dEa[0] ? P.dEb[q] : P.dEa[q]);
+                const int n = fmx::launch_march3d_sweeps2<T>(g->geo, c, dp, in, out, g->stream, last);
+                if (n) {
+                    g->launches += n;
+                    ++it;  // two sweeps done
+                    if (last) {
+                        updated = true;
+                        break;
+                    }
+                    for (int q = 0; q < 3; ++q) in[q] = out[q];
+                    continue;
+                }
+            }
             // the z-marching FP32 sweep can apply E^{n+1} = E^n + dE in its last pass
             if (march && it == g->p.m - 1) {
                 const int n = fmx::launch_march3d_sweep<T>(g->geo, c, dp, in, P.E, g->stream, true);
@@ -454,7 +474,7 @@ fmx_status staged_step(fmx_grid *g) {
                 }
             }
             T *out[3];
-            for (int q = 0; q < 3; ++q) out[q] = (it % 2 == 0) ? P.dEa[q] : P.dEb[q];
+            for (int q = 0; q < 3; ++q) out[q] = in[0] == P.dEa[0] ? P.dEb[q] : P.dEa[q];
             g->launches += march ? fmx::launch_march3d_sweep<T>(g->geo, c, dp, in, out, g->stream)
                                  : fmx::launch_staged_sweep<T>(g->geo, g->p.dims, c, P, in, out, false, g->stream);
             for (int q = 0; q < 3; ++q) in[q] = out[q];
@@ -1350,6 +1370,22 @@ fmx_status fmx_profile_read(fmx_grid *g, fmx_kernel_stat *out, int max, int *n) 
     }
     g->ev_used = 0;
     return FMX_OK;
+}
+
+fmx_status fmx_set_option(fmx_grid *g, int option, int value) {
+    if (!g) return fail(FMX_EINVAL, "NULL grid");
+    switch (option) {
+        case FMX_OPT_SWEEPS_PER_PASS:
+            if (value != 1 && value != 2) return fail(FMX_EINVAL, "sweeps per pass must be 1 or 2 (got %d)", value);
+            g->sweeps_per_pass = value;
+            return FMX_OK;
+    }
+    return fail(FMX_EINVAL, "unknown option %d", option);
+}
+
+int fmx_get_option(const fmx_grid *g, int option) {
+    if (!g) return -1;
+    return option == FMX_OPT_SWEEPS_PER_PASS ? g->sweeps_per_pass : -1;
 }
 
 fmx_status fmx_step_host(fmx_grid *g, const fmx_host_step *io, int count) {

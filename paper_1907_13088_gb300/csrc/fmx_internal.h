@@ -109,6 +109,12 @@ int launch_march3d_source(const Geo &g, const Coef<T> &c, const T *const B[3], c
 template <typename T>
 int launch_march3d_sweep(const Geo &g, const Coef<T> &c, const T *const dEp[3], const T *const in[3], T *const out[3],
                          cudaStream_t s, bool update = false);
+// Two sweeps of Algorithm 1 in one z-march pass (FP32 column pairs); with
+// update the second applies E^{n+1} = E^n + dE into out.  Returns 0 (nothing
+// launched) where that path does not apply.
+template <typename T>
+int launch_march3d_sweeps2(const Geo &g, const Coef<T> &c, const T *const dEp[3], const T *const in[3],
+                           T *const out[3], cudaStream_t s, bool update);
 // Faraday of the 3D FP32 column-pair path; returns 0 (nothing launched) where
 // that path does not apply
 template <typename T>

@@ -636,6 +636,130 @@ __global__ void __launch_bounds__(NTH, 3) k3_faraday2(Geo g, Coef3P c, const flo
     cp_async_wait<0>();
 }
 
+// ---------------------------------------------------------------------------
+// Two sweeps of Algorithm 1 in one z-march (temporal blocking, FP32 column
+// pairs, even n_x): dE_(s+2) = dE' + A (dE' + A dE_(s)).  The first sweep (A
+// stage) is evaluated on the output tile grown by one cell on every side in
+// x and y (34 pairs x 10 rows around the 32 x 8 pairs of the tile), from an
+// input ring whose planes carry a halo of two; its results stay in a second
+// shared-memory ring that the second sweep (B stage) reads two planes behind,
+// so dE_(s+1) never leaves the SM.  352 threads: every thread but the last 12
+// owns a first-sweep pair, the first 256 also the second-sweep pair of the
+// tile.  One barrier per plane.  With UPD the second sweep also applies
+// E^{n+1} = E^n + dE (E in place).
+constexpr int FRW = 72;                // floats per row: column x0 + j at index j + 4, j in [-4, 67]
+constexpr int FIR = 12, FAR = 10;      // rows of an input plane (y0-2..y0+9) and of a first-sweep plane (y0-1..y0+8)
+constexpr int FIPL = FRW * FIR, FAPL = FRW * FAR;
+constexpr int FNT = 352, FNA = 340, FNB = 256;
+constexpr int FRS = 8, FLA = FRS - 3;  // input ring slots, planes in flight
+constexpr int FAS = 4;                 // first-sweep ring slots
+constexpr int FNI = (FRW / 2) * FIR;   // pair copies per input plane and component (432)
+
+template <bool UPD>
+__global__ void __launch_bounds__(FNT, 1) k3_sweeps2f(Geo g, Coef3P c, const float *p0, const float *p1,
+                                                     const float *p2, const float *i0, const float *i1,
+                                                     const float *i2, float *o0, float *o1, float *o2) {
+    using namespace pair2;
+    extern __shared__ __align__(16) unsigned char m3raw[];
+    float *ring = reinterpret_cast<float *>(m3raw);  // [FRS][3][FIPL] input planes, halo 2
+    float *aring = ring + FRS * 3 * FIPL;             // [FAS][3][FAPL] first-sweep planes, halo 1
+    const float *in[3] = {i0, i1, i2};
+    const float *dp[3] = {p0, p1, p2};
+    float *out[3] = {o0, o1, o2};
+    const int x0 = blockIdx.x * TX2, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * ZSEG, z1 = min(z0 + ZSEG, g.nz);
+    const int tid = threadIdx.x;
+    // input copy items of this thread (pairs of columns, periodic wrap)
+    int cs[2], co[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int q = tid + r * FNT;
+        cs[r] = -1;
+        co[r] = 0;
+        if (q < FNI) {
+            const int row = q / (FRW / 2), j = 2 * (q % (FRW / 2)) - 4;
+            cs[r] = row * FRW + j + 4;
+            co[r] = wrapm(y0 - 2 + row, g.ny) * (int)g.pitch + wrapm(x0 + j, g.nx);
+        }
+    }
+    auto issue_plane = [&](int k) {
+        const int64_t base = (int64_t)wrapm(k, g.nz) * g.plane;
+        float *slot = ring + (k & (FRS - 1)) * 3 * FIPL;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            if (cs[r] < 0) continue;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) cp_async_pair(slot + q * FIPL + cs[r], in[q] + base + co[r]);
+        }
+    };
+    // copy group m: input planes z0-2..z0 (m = 0), plane z0+m (m >= 1, up to z1+1)
+    auto issue = [&](int m) {
+        if (m == 0) {
+            issue_plane(z0 - 2);
+            issue_plane(z0 - 1);
+            issue_plane(z0);
+        } else if (z0 + m <= z1 + 1) {
+            issue_plane(z0 + m);
+        }
+        cp_async_commit();
+    };
+    // first-sweep pair (A stage) and second-sweep pair (B stage) of this thread
+    const bool hasA = tid < FNA, hasB = tid < FNB;
+    const int pa = tid % 34 - 1, ra = tid / 34 - 1;  // pair -1..32, row -1..8
+    const int pb = tid % 32, rb = tid / 32;          // pair 0..31, row 0..7
+    const int ca = 2 * pa + 4, cb = 2 * pb + 4;      // smem column of the own pair
+    const int64_t cellA = (int64_t)wrapm(y0 + ra, g.ny) * g.pitch + wrapm(x0 + 2 * pa, g.nx);
+    const int64_t cellB = (int64_t)(y0 + rb) * g.pitch + (x0 + 2 * pb);
+    const bool outB = hasB && x0 + 2 * pb < g.nx && y0 + rb < g.ny;
+    auto ld2 = [&](const float *base, int k, int64_t cell) {
+        return *reinterpret_cast<const float2 *>(base + (int64_t)wrapm(k, g.nz) * g.plane + cell);
+    };
+#pragma unroll
+    for (int m = 0; m < FLA; ++m) issue(m);
+    for (int k = z0 - 1; k <= z1 + 1; ++k) {
+        const int it = k - (z0 - 1);
+        cp_async_wait<FLA - 1>();
+        __syncthreads();
+        issue(it + FLA);
+        // A stage: dE_(s+1) of plane k on the grown tile
+        if (hasA && k <= z1) {
+            const int sm1 = ((k - 1) & (FRS - 1)) * 3 * FIPL, s0 = (k & (FRS - 1)) * 3 * FIPL,
+                      sp1 = ((k + 1) & (FRS - 1)) * 3 * FIPL;
+            const int cA = (ra + 2) * FRW + ca;
+            auto V = [&](int q, int dx, int dy, int dz) -> f2 {
+                const float *row = ring + (dz < 0 ? sm1 : (dz > 0 ? sp1 : s0)) + q * FIPL + cA + dy * FRW;
+                const f2 pr = *reinterpret_cast<const float2 *>(row);
+                return dx == 0 ? pr : (dx > 0 ? mk(pr.y, row[2]) : mk(row[-1], pr.x));
+            };
+            float *dst = aring + (k & (FAS - 1)) * 3 * FAPL + (ra + 1) * FRW + ca;
+            *reinterpret_cast<float2 *>(dst) = add(ld2(dp[0], k, cellA), apply_a2<0>(V, c));
+            *reinterpret_cast<float2 *>(dst + FAPL) = add(ld2(dp[1], k, cellA), apply_a2<1>(V, c));
+            *reinterpret_cast<float2 *>(dst + 2 * FAPL) = add(ld2(dp[2], k, cellA), apply_a2<2>(V, c));
+        }
+        // B stage: dE_(s+2) of plane k-2 on the tile, from first-sweep planes k-3..k-1
+        const int kb = k - 2;
+        if (outB && kb >= z0 && kb < z1) {
+            const int sm1 = ((kb - 1) & (FAS - 1)) * 3 * FAPL, s0 = (kb & (FAS - 1)) * 3 * FAPL,
+                      sp1 = ((kb + 1) & (FAS - 1)) * 3 * FAPL;
+            const int cB = (rb + 1) * FRW + cb;
+            auto V = [&](int q, int dx, int dy, int dz) -> f2 {
+                const float *row = aring + (dz < 0 ? sm1 : (dz > 0 ? sp1 : s0)) + q * FAPL + cB + dy * FRW;
+                const f2 pr = *reinterpret_cast<const float2 *>(row);
+                return dx == 0 ? pr : (dx > 0 ? mk(pr.y, row[2]) : mk(row[-1], pr.x));
+            };
+            f2 r[3] = {add(ld2(dp[0], kb, cellB), apply_a2<0>(V, c)), add(ld2(dp[1], kb, cellB), apply_a2<1>(V, c)),
+                       add(ld2(dp[2], kb, cellB), apply_a2<2>(V, c))};
+            const int64_t idx = (int64_t)kb * g.plane + cellB;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                if (UPD) r[q] = add(*reinterpret_cast<const float2 *>(out[q] + idx), r[q]);
+                *reinterpret_cast<float2 *>(out[q] + idx) = r[q];
+            }
+        }
+    }
+    cp_async_wait<0>();
+}
+
 inline dim3 grid3(const Geo &g) { return dim3((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + ZSEG - 1) / ZSEG); }
 
 }  // namespace
@@ -706,6 +830,33 @@ void run_sweep2(const Geo &g, const Coef<float> &c, const float *const dEp[3], c
                                                      out[1], out[2]);
 }
 
+template <bool UPD>
+void run_sweeps2f(const Geo &g, const Coef<float> &c, const float *const dEp[3], const float *const in[3],
+                  float *const out[3], cudaStream_t s) {
+    constexpr size_t bytes = ((size_t)FRS * 3 * FIPL + (size_t)FAS * 3 * FAPL) * sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k3_sweeps2f<UPD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        attr = true;
+    }
+    const dim3 grid((g.nx + TX2 - 1) / TX2, (g.ny + TY - 1) / TY, (g.nz + ZSEG - 1) / ZSEG);
+    k3_sweeps2f<UPD><<<grid, FNT, bytes, s>>>(g, coef3p(c), dEp[0], dEp[1], dEp[2], in[0], in[1], in[2], out[0],
+                                             out[1], out[2]);
+}
+
+template <typename T>
+int launch_march3d_sweeps2(const Geo &g, const Coef<T> &c, const T *const dEp[3], const T *const in[3],
+                           T *const out[3], cudaStream_t s, bool update) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (pair_path(g, (float *)nullptr)) {
+            if (update) run_sweeps2f<true>(g, c, dEp, in, out, s);
+            else run_sweeps2f<false>(g, c, dEp, in, out, s);
+            return 1;
+        }
+    }
+    return 0;  // FP64, odd n_x or a small grid: the caller runs the sweeps one per pass
+}
+
 template <typename T>
 int launch_march3d_source(const Geo &g, const Coef<T> &c, const T *const B[3], const T *const J[3], int passes,
                           T *const out[3], cudaStream_t s) {
@@ -767,7 +918,9 @@ int launch_march3d_sweep(const Geo &g, const Coef<T> &c, const T *const dEp[3], 
                                           T *const[3], cudaStream_t);                                           \
     template int launch_march3d_sweep<T>(const Geo &, const Coef<T> &, const T *const[3], const T *const[3],       \
                                          T *const[3], cudaStream_t, bool);                                        \
-    template int launch_march3d_faraday<T>(const Geo &, const Coef<T> &, const T *const[3], T *const[3], cudaStream_t);
+    template int launch_march3d_faraday<T>(const Geo &, const Coef<T> &, const T *const[3], T *const[3], cudaStream_t); \
+    template int launch_march3d_sweeps2<T>(const Geo &, const Coef<T> &, const T *const[3], const T *const[3],    \
+                                           T *const[3], cudaStream_t, bool);
 FMX_M3_INST(float)
 FMX_M3_INST(double)
 #undef FMX_M3_INST

@@ -130,6 +130,8 @@ def _load():
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
         "fmx_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
         "fmx_step_host": (ctypes.c_int, [G, ctypes.POINTER(fmx_host_step), ctypes.c_int]),
+        "fmx_set_option": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_int]),
+        "fmx_get_option": (ctypes.c_int, [G, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -186,6 +188,9 @@ fmx_profile_read = _lib.fmx_profile_read
 fmx_nci_resonance = _lib.fmx_nci_resonance
 fmx_fma_peak = _lib.fmx_fma_peak
 fmx_step_host = _lib.fmx_step_host
+fmx_set_option = _lib.fmx_set_option
+fmx_get_option = _lib.fmx_get_option
+FMX_OPT_SWEEPS_PER_PASS = 1
 FMX_STATIC_SCRATCH_BYTES = 4 << 20
 
 
@@ -351,6 +356,12 @@ class Grid:
     # -- work ------------------------------------------------------------
     def step(self, nsteps=1):
         check(fmx_step(self.handle, int(nsteps)), "fmx_step")
+
+    def set_option(self, option, value):
+        check(fmx_set_option(self.handle, int(option), int(value)), "fmx_set_option")
+
+    def get_option(self, option) -> int:
+        return int(fmx_get_option(self.handle, int(option)))
 
     def step_host(self, steps):
         """fmx_step_host: ``steps`` is a list of (inputs, outputs), inputs a

@@ -100,8 +100,18 @@ def test_validation_codes(fmx):
     assert fmx.create_status(fmx.make_params((64, 64), filter_passes=1, filter_target=fmx.FMX_FILTER_FIELDS,
                                              engine=R))[0] == fmx.FMX_EUNSUPPORTED
     assert fmx.create_status(fmx.make_params((16, 16), engine=4))[0] == fmx.FMX_EINVAL
-    # the FMA-rate measurement refuses bad arguments before any device work
+    # per-grid kernel options (host only)
     import ctypes
+    h = ctypes.c_void_p()
+    q = fmx.make_params((32, 32, 32), m=4)
+    assert fmx.fmx_create(ctypes.byref(q), ctypes.byref(h), None) == fmx.FMX_OK
+    assert fmx.fmx_get_option(h, fmx.FMX_OPT_SWEEPS_PER_PASS) == 1
+    assert fmx.fmx_set_option(h, fmx.FMX_OPT_SWEEPS_PER_PASS, 2) == fmx.FMX_OK
+    assert fmx.fmx_get_option(h, fmx.FMX_OPT_SWEEPS_PER_PASS) == 2
+    assert fmx.fmx_set_option(h, fmx.FMX_OPT_SWEEPS_PER_PASS, 3) == fmx.FMX_EINVAL
+    assert fmx.fmx_set_option(h, 99, 1) == fmx.FMX_EINVAL and fmx.fmx_get_option(h, 99) == -1
+    fmx.fmx_destroy(h)
+    # the FMA-rate measurement refuses bad arguments before any device work
     out = ctypes.c_double(0.0)
     assert fmx.fmx_fma_peak(7, None, ctypes.byref(out)) == fmx.FMX_EINVAL
     assert fmx.fmx_fma_peak(fmx.FMX_F64, None, None) == fmx.FMX_EINVAL
