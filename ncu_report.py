@@ -1,11 +1,12 @@
-"""Summaries of Nsight Compute output for the kernels of this package.
+"""Summaries of Nsight Compute output for the kernels of the field-advance
+library (measurement tooling beside bench.py, not part of the library).
 
-    python -m paper_1907_13088_gb300.ncu_report launches launches.csv
+    python ncu_report.py launches launches.csv
         per-kernel launches, total device time and share from a launch list
         (ncu --metrics gpu__time_duration.sum --csv --log-file launches.csv ...)
-    python -m paper_1907_13088_gb300.ncu_report full raw.csv
+    python ncu_report.py full raw.csv
         key counters per captured launch from `ncu -i rep --page raw --csv`
-    python -m paper_1907_13088_gb300.ncu_report traffic raw.csv out.json
+    python ncu_report.py traffic raw.csv out.json
         dram bytes (read + write) per launch of each TE / TM kernel, stored
         with the hash of the kernel sources they were taken on (bench.py
         reports them as `traffic` only while the hash still matches)
@@ -22,6 +23,7 @@ import os
 import sys
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
+_CSRC = os.path.join(_HERE, "paper_1907_13088_gb300", "csrc")
 KERNEL_SOURCES = ("fused2d_pol.cu", "pol_tile.cuh", "pair2.cuh", "fused2d.h", "fmx_internal.h")
 
 
@@ -29,7 +31,7 @@ def kernel_hash() -> str:
     """First 16 hex digits of the sha256 of the TE / TM kernel sources."""
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
-        with open(os.path.join(_HERE, "csrc", name), "rb") as f:
+        with open(os.path.join(_CSRC, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 

@@ -646,17 +646,21 @@ __global__ void __launch_bounds__(NTH, 3) k3_faraday2(Geo g, Coef3P c, const flo
 // so dE_(s+1) never leaves the SM.  352 threads: every thread but the last 12
 // owns a first-sweep pair, the first 256 also the second-sweep pair of the
 // tile.  One barrier per plane.  With UPD the second sweep also applies
-// E^{n+1} = E^n + dE (E in place).
+// E^{n+1} = E^n + dE (E in place).  Two CTAs per SM (80 registers, 76 KB of
+// shared memory, one input plane in flight) measured faster than one CTA
+// with five planes in flight (256^3: 1.60 vs 1.83 ms per step); both are
+// slower than one sweep per pass (1.06 ms): the grown tile and the lower
+// occupancy cost more on-chip work than the saved HBM traffic returns.
 constexpr int FRW = 72;                // floats per row: column x0 + j at index j + 4, j in [-4, 67]
 constexpr int FIR = 12, FAR = 10;      // rows of an input plane (y0-2..y0+9) and of a first-sweep plane (y0-1..y0+8)
 constexpr int FIPL = FRW * FIR, FAPL = FRW * FAR;
 constexpr int FNT = 352, FNA = 340, FNB = 256;
-constexpr int FRS = 8, FLA = FRS - 3;  // input ring slots, planes in flight
+constexpr int FRS = 4, FLA = FRS - 3;  // input ring slots, planes in flight (2 CTAs per SM)
 constexpr int FAS = 4;                 // first-sweep ring slots
 constexpr int FNI = (FRW / 2) * FIR;   // pair copies per input plane and component (432)
 
 template <bool UPD>
-__global__ void __launch_bounds__(FNT, 1) k3_sweeps2f(Geo g, Coef3P c, const float *p0, const float *p1,
+__global__ void __launch_bounds__(FNT, 2) k3_sweeps2f(Geo g, Coef3P c, const float *p0, const float *p1,
                                                      const float *p2, const float *i0, const float *i1,
                                                      const float *i2, float *o0, float *o1, float *o2) {
     using namespace pair2;

@@ -97,18 +97,57 @@ def _mode_norm(shape):
     return np.sqrt(mx * mx + my * my + mz * mz)
 
 
-def power_law_fields(shape, kmax, seed, exponent=-2.0, dtype=np.float32):
-    """E and B with random-phase spectra, |field|^2 power proportional to
-    |n|^exponent over the integer mode vectors 1 <= |n| <= kmax, each component
-    independent and of unit RMS.  Returns (E, B)."""
+def _back(f, axis):
+    """f[i] - f[i-1] along a grid axis (x = 2, y = 1, z = 0 of the array)."""
+    if f.shape[axis] == 1:
+        return np.zeros_like(f)
+    return f - np.roll(f, 1, axis=axis)
+
+
+def _fwd(f, axis):
+    """f[i+1] - f[i] along a grid axis."""
+    if f.shape[axis] == 1:
+        return np.zeros_like(f)
+    return np.roll(f, -1, axis=axis) - f
+
+
+def _curl_back(p, d):
+    """Staggered curl with backward differences: a potential at the B
+    positions to a field at the E positions (zero backward divergence)."""
+    return np.stack([_back(p[2], 1) / d[1] - _back(p[1], 0) / d[2],
+                     _back(p[0], 0) / d[2] - _back(p[2], 2) / d[0],
+                     _back(p[1], 2) / d[0] - _back(p[0], 1) / d[1]])
+
+
+def _curl_fwd(p, d):
+    """Staggered curl with forward differences: a potential at the E
+    positions to a field at the B positions (zero forward divergence)."""
+    return np.stack([_fwd(p[2], 1) / d[1] - _fwd(p[1], 0) / d[2],
+                     _fwd(p[0], 0) / d[2] - _fwd(p[2], 2) / d[0],
+                     _fwd(p[1], 2) / d[0] - _fwd(p[0], 1) / d[1]])
+
+
+def power_law_fields(shape, kmax, seed, exponent=-2.0, dtype=np.float32, d=(1.0, 1.0, 1.0)):
+    """Divergence-free E and B with random-phase spectra: E = C^T psi_E (the
+    backward staggered curl of a potential at the B positions), B = C psi_B
+    (the forward curl of a potential at the E positions), so that the
+    backward divergence of E and the forward divergence of B vanish
+    identically.  Each potential component has amplitude |n|^(exponent/2 - 1)
+    on the integer mode vectors 1 <= |n| <= kmax, so the fields' power falls
+    as |n|^exponent there (the curl contributes one power of |n|) and is zero
+    elsewhere; E and B are each scaled to unit RMS over their three
+    components.  Returns (E, B)."""
     s = _shape3(shape)
     nrm = _mode_norm(s)
-    w = np.where((nrm >= 1.0) & (nrm <= kmax), np.power(np.maximum(nrm, 1.0), exponent / 2.0), 0.0)
+    w = np.where((nrm >= 1.0) & (nrm <= kmax), np.power(np.maximum(nrm, 1.0), exponent / 2.0 - 1.0), 0.0)
     rng = np.random.default_rng(seed)
-    out = np.empty((6,) + (s[2], s[1], s[0]), dtype=dtype)
-    for c in range(6):
-        out[c] = _spectrum_plane(rng, s, w, dtype)
-    return out[:3].copy(), out[3:].copy()
+    out = []
+    for curl in (_curl_back, _curl_fwd):
+        psi = [_spectrum_plane(rng, s, w, np.float64) for _ in range(3)]
+        F = curl(psi, d)
+        r = float(np.sqrt(np.mean(F * F)))
+        out.append((F / r if r > 0 else F).astype(dtype))
+    return out[0], out[1]
 
 
 def solenoidal_current(shape, seed, width=16.0, rms=1e-3, dtype=np.float32, d=(1.0, 1.0, 1.0)):
@@ -127,16 +166,7 @@ def solenoidal_current(shape, seed, width=16.0, rms=1e-3, dtype=np.float32, d=(1
     w[0, 0, 0] = 0.0
     rng = np.random.default_rng(seed)
     psi = [_spectrum_plane(rng, s, w, np.float64) for _ in range(3)]
-
-    def back(f, axis):  # f[i] - f[i-1] along a grid axis (x=2, y=1, z=0 of the array)
-        if f.shape[axis] == 1:
-            return np.zeros_like(f)
-        return f - np.roll(f, 1, axis=axis)
-
-    jx = back(psi[2], 1) / d[1] - back(psi[1], 0) / d[2]
-    jy = back(psi[0], 0) / d[2] - back(psi[2], 2) / d[0]
-    jz = back(psi[1], 2) / d[0] - back(psi[0], 1) / d[1]
-    J = np.stack([jx, jy, jz])
+    J = _curl_back(psi, d)
     r = float(np.sqrt(np.mean(J ** 2)))
     if r > 0:
         J *= rms / r

@@ -56,7 +56,8 @@ def test_profile_commands_run_committed_files():
     resource report: the summaries stay reproducible from committed files."""
     import shlex
     b = _bench()
-    from paper_1907_13088_gb300 import build, ncu_report
+    import ncu_report
+    from paper_1907_13088_gb300 import build
     cmds = _commands()
     assert len(cmds) >= 8
     seen_bench = 0
@@ -66,8 +67,8 @@ def test_profile_commands_run_committed_files():
             args = words[words.index("bench.py") + 1:]
             b._parser().parse_args(args)  # raises SystemExit on an unknown option
             seen_bench += 1
-        if "paper_1907_13088_gb300.ncu_report" in words:
-            mode = words[words.index("paper_1907_13088_gb300.ncu_report") + 1]
+        if "ncu_report.py" in words:
+            mode = words[words.index("ncu_report.py") + 1]
             assert hasattr(ncu_report, mode), (name, mode)
         if "paper_1907_13088_gb300.build" in words:
             assert "--resources" in words and hasattr(build, "resources"), (name, cmd)

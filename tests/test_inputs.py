@@ -19,15 +19,34 @@ def test_power_law_fields_support_rms_and_slope():
     nrm = _mode_norm_2d(nx, ny)
     outside = (nrm < 1.0) | (nrm > kmax)
     shells = np.arange(2, kmax + 1)
-    for f in list(E) + list(B):
-        f = f[0]
-        assert abs(math.sqrt(np.mean(f * f)) - 1.0) < 1e-6  # unit RMS (spectrum built in complex64)
-        P = np.abs(np.fft.fft2(f)) ** 2
-        assert P[outside].max() < 1e-10 * P.max()  # only 1 <= |n| <= k_max
-        # shell-averaged power falls as |n|^-2 (random phases: on average)
-        mean = np.array([P[(nrm >= r - 0.5) & (nrm < r + 0.5)].mean() for r in shells])
-        slope = np.polyfit(np.log(shells), np.log(mean), 1)[0]
-        assert abs(slope + 2.0) < 0.2, slope
+    for F in (E, B):
+        assert abs(math.sqrt(np.mean(F * F)) - 1.0) < 1e-12  # unit RMS over the three components
+        for f in F:
+            f = f[0]
+            P = np.abs(np.fft.fft2(f)) ** 2
+            assert P[outside].max() < 1e-10 * P.max()  # only 1 <= |n| <= k_max
+            # shell-averaged power falls as |n|^-2 (random phases: on average)
+            mean = np.array([P[(nrm >= r - 0.5) & (nrm < r + 0.5)].mean() for r in shells])
+            slope = np.polyfit(np.log(shells), np.log(mean), 1)[0]
+            assert abs(slope + 2.0) < 0.25, slope
+
+
+def _fwd_div(B, d):
+    """Forward-difference divergence on the periodic grid (arrays (3, nz, ny, nx))."""
+    div = np.zeros(B.shape[1:])
+    for a, axis in ((0, 2), (1, 1), (2, 0)):
+        if B.shape[1 + axis] > 1:
+            div += (np.roll(B[a], -1, axis=axis) - B[a]) / d[a]
+    return div
+
+
+def test_power_law_fields_are_divergence_free():
+    """E = C^T psi_E has zero backward divergence, B = C psi_B zero forward
+    divergence (the divergence of the Faraday update), to round-off."""
+    for shape, d in (((64, 48), (1.0, 1.0, 1.0)), ((16, 12, 10), (1.0, 0.8, 1.2))):
+        E, B = synth.power_law_fields(shape, 6, seed=3, dtype=np.float64, d=d)
+        assert np.abs(_back_div(E, d)).max() < 1e-12 * np.abs(E).max()
+        assert np.abs(_fwd_div(B, d)).max() < 1e-12 * np.abs(B).max()
 
 
 def _back_div(J, d):

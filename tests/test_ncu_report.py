@@ -4,7 +4,7 @@ aggregation and shares) is checked here on small hand-made files in ncu's
 column layout (no GPU, no ncu)."""
 import json
 
-from paper_1907_13088_gb300 import ncu_report
+import ncu_report
 
 LAUNCH_HDR = ('"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size",'
               '"Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"')
