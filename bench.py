@@ -355,6 +355,15 @@ def run_batch(args):
     cells = sum(a * b for a, b in shapes)
     bt = fmx.Batch(shapes, cfs, m=4)
     chosen = bt.tune(trial_steps=10)
+    tiles = bt.tiles()
+    # grid-size classes of the tuned work list: which grids run on narrow tiles
+    narrow_grids = [i for i in range(len(shapes)) if bt.grid_width(i) < 200]
+    size_classes = {}
+    for i, (a, b_) in enumerate(shapes):
+        cls = "nx<128" if a < 128 else ("nx<256" if a < 256 else ("nx<512" if a < 512 else "nx>=512"))
+        d = size_classes.setdefault(cls, {"grids": 0, "narrow_tiles": 0})
+        d["grids"] += 1
+        d["narrow_tiles"] += int(i in narrow_grids)
     fields = [synth.power_law_fields(sh, max(2, min(sh) // 8), 1907004 + i) for i, sh in enumerate(shapes)]
     for i, (E, B) in enumerate(fields):
         bt.set_fields(i, E, B)
@@ -406,6 +415,10 @@ def run_batch(args):
                                "(seed 1907004), Courant U[0.3, 0.9], FP32, vacuum, m = 4, one persistent launch "
                                "per step replayed from CUDA graphs, autotuned tile rows",
                    "cells_total": cells, "grids": len(shapes), "tuned_tile_rows": chosen or "auto",
+                   "tuned_tile_rule": {0: "wide tiles only", 1: "narrow tiles where they compute fewer columns",
+                                       2: "narrow tiles everywhere"}[tiles["narrow_rule"]],
+                   "tiles": {"wide": tiles["wide"], "narrow": tiles["narrow"], "single_column": tiles["single"]},
+                   "size_classes": size_classes,
                    "work_items": bt.items, "single_grid_path_gcells": round(single, 3)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,

@@ -354,12 +354,36 @@ fmx_status fmx_batch_get_fields(fmx_batch *b, int i, unsigned mask, void *const 
  * the work list outgrows the workspace, FMX_ECUDA) unbinds the batch. */
 fmx_status fmx_batch_set_rows(fmx_batch *b, int rows);
 
-/* Autotuner: times each candidate row extent (automatic, 1024, 512, 256, 128,
- * 64, 32) over `trial_steps` graph-replayed steps with CUDA events, keeps
- * the fastest and returns it in *chosen (0 = automatic; chosen may be NULL).
- * The trial steps advance the grids' state: set the fields afterwards.
- * Errors: FMX_EINVAL (trial_steps < 2), FMX_ESTATE (not bound), FMX_ECUDA,
- * and those of fmx_batch_set_rows. */
+/* Tile widths of the column-pair kernels: a CTA of 128 threads runs either
+ * one wide tile (256 columns) or two narrow tiles of 128 columns side by
+ * side (half the CTA each), all in the same persistent launch.  Rule 0: wide
+ * tiles only; 1 (default): narrow tiles for the grids where they compute
+ * fewer columns than wide ones (grids narrower than about 114 columns, and
+ * widths that leave a wide strip mostly empty); 2: narrow tiles for every
+ * grid.  Rebuilds the work list like fmx_batch_set_rows (same errors); no
+ * result depends on it. */
+fmx_status fmx_batch_set_tiles(fmx_batch *b, int narrow_rule);
+
+/* The current work list: wide and narrow tiles of the column-pair kernels,
+ * tiles of the single-column kernel (lumped grids), the rows rule
+ * (fmx_batch_set_rows) and the tile rule (fmx_batch_set_tiles); any pointer
+ * may be NULL.  Errors: FMX_EINVAL (NULL batch), FMX_ESTATE (not bound). */
+fmx_status fmx_batch_tiles(const fmx_batch *b, int *wide, int *narrow, int *single, int *rows, int *narrow_rule);
+
+/* Columns one tile of grid i writes in the current work list (wide or
+ * narrow column-pair tile, or the single-column tile), or -1 (NULL batch,
+ * not bound, i out of range). */
+int fmx_batch_grid_width(const fmx_batch *b, int i);
+
+/* Autotuner: times every pair of tile rule (1, then 0) and row extent
+ * (automatic, 1024, 512, 256, 128, 64, 32) over `trial_steps` graph-replayed
+ * steps with CUDA events, keeps the fastest pair and returns its row extent
+ * in *chosen (0 = automatic; chosen may be NULL; fmx_batch_tiles reports
+ * both).  The choice is cached in the process by the batch's signature (m,
+ * filter passes, current, every grid's size): a later batch of the same grids
+ * takes it without trial steps.  The trial steps advance the grids' state:
+ * set the fields afterwards.  Errors: FMX_EINVAL (trial_steps < 2),
+ * FMX_ESTATE (not bound), FMX_ECUDA, and those of fmx_batch_set_rows. */
 fmx_status fmx_batch_tune(fmx_batch *b, int trial_steps, int *chosen);
 
 /* Enqueues nsteps steps of every grid (graph replays plus at most one

@@ -12,6 +12,9 @@
 
 #include <new>
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "fmx.h"
@@ -1570,6 +1573,11 @@ struct fmx_batch {
     bool pol_ok = false;
     int pwidth = 0, pbps = 1;
     size_t psmem = 0;
+    // narrow tiles (half a CTA each, two per CTA) and the rule that picks them
+    int pwidth_n = 0;
+    size_t pnbytes = 0;
+    int narrow_policy = 1;
+    int nwide = 0, nnarrow = 0;
     bool bound = false;
     fmx::BatchGrid *d_grids = nullptr;
     fmx::BatchItem *d_items = nullptr;  // pol items, then single-column items
@@ -1614,15 +1622,27 @@ bool batch_pol_grid(const fmx_batch *b, int i) {
     return b->pol_ok && G.c.c6 == 1.f / 6.f && (int64_t)G.g.ny * G.g.pitch < ((int64_t)1 << 31);
 }
 
+// Whether a grid of the polarisation kernels takes narrow tiles: never
+// (policy 0), where they compute fewer columns than wide ones (policy 1), or
+// always (policy 2).
+bool batch_narrow(const fmx_batch *b, int i) {
+    if (b->narrow_policy == 0 || b->pwidth_n <= 0) return false;
+    if (b->narrow_policy == 2) return true;
+    const int nx = (int)b->p[i].n[0];
+    const int64_t wide = (int64_t)((nx + b->pwidth - 1) / b->pwidth) * 2 * b->threads;
+    const int64_t narrow = (int64_t)((nx + b->pwidth_n - 1) / b->pwidth_n) * b->threads;
+    return narrow < wide;
+}
+
 fmx_status batch_build(fmx_batch *b) {
-    std::vector<fmx::BatchItem> items[2];  // [0] pol, [1] single column
-    std::vector<double> cost[2];
+    std::vector<fmx::BatchItem> items[3];  // [0] wide pol, [1] narrow pol, [2] single column
+    std::vector<double> cost[3];
     const int warm = 3 * b->m + 2 * b->passes + 8;
     for (int i = 0; i < b->n; ++i) {
         fmx::BatchGrid &G = b->grids[i];
-        const int kind = batch_pol_grid(b, i) ? 0 : 1;
+        const int kind = batch_pol_grid(b, i) ? (batch_narrow(b, i) ? 1 : 0) : 2;
         G.L = batch_rows(b, i);
-        G.W = kind == 0 ? b->pwidth : b->width;
+        G.W = kind == 0 ? b->pwidth : (kind == 1 ? b->pwidth_n : b->width);
         G.nstrip = (G.g.nx + G.W - 1) / G.W;
         const int nseg = (G.g.ny + G.L - 1) / G.L;
         for (int st = 0; st < G.nstrip; ++st)
@@ -1632,17 +1652,20 @@ fmx_status batch_build(fmx_batch *b) {
                 cost[kind].push_back((double)rows + warm);
             }
     }
-    if (items[0].size() + items[1].size() > b->max_items)
+    if (items[0].size() + items[1].size() + items[2].size() > b->max_items)
         return fail(FMX_EINVAL, "batch work list larger than its workspace");
-    // each list longest tiles first
+    // each list longest tiles first (narrow tiles pair up with their neighbours
+    // in this order, so the two halves of a CTA get similar row counts)
     std::vector<fmx::BatchItem> sorted;
-    for (int kind = 0; kind < 2; ++kind) {
+    for (int kind = 0; kind < 3; ++kind) {
         std::vector<size_t> order(items[kind].size());
         for (size_t k = 0; k < order.size(); ++k) order[k] = k;
         std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[kind][x] > cost[kind][y]; });
         for (size_t k = 0; k < order.size(); ++k) sorted.push_back(items[kind][order[k]]);
     }
-    b->npol = (int)items[0].size();
+    b->nwide = (int)items[0].size();
+    b->nnarrow = (int)items[1].size();
+    b->npol = b->nwide + b->nnarrow;
     b->nitems = (int)sorted.size();
     cudaError_t e = cudaMemcpyAsync(b->d_grids, b->grids.data(), sizeof(fmx::BatchGrid) * b->n,
                                     cudaMemcpyHostToDevice, b->stream);
@@ -1660,9 +1683,10 @@ fmx_status batch_build(fmx_batch *b) {
 fmx_status batch_launch(fmx_batch *b, int parity) {
     const int nscal = b->nitems - b->npol;
     if (b->npol > 0) {
-        const int slots = b->pbps * b->sms, want = 2 * b->npol;
-        const int nl = fmx::launch_fused2d_pol_batch(b->m, b->passes, b->hj, b->d_grids, b->d_items, b->npol, parity,
-                                                     want < slots ? want : slots, b->psmem, b->stream);
+        const int slots = b->pbps * b->sms, want = 2 * (b->nwide + (b->nnarrow + 1) / 2);
+        const int nl = fmx::launch_fused2d_pol_batch(b->m, b->passes, b->hj, b->d_grids, b->d_items, b->nwide,
+                                                     b->nnarrow, parity, want < slots ? want : slots, b->psmem,
+                                                     b->pnbytes, b->stream);
         if (nl < 0) return fail(FMX_EUNSUPPORTED, "batched kernel not instantiated");
         b->launches += nl;
     }
@@ -1751,7 +1775,8 @@ fmx_status fmx_batch_create(const fmx_params *ps, int n, fmx_batch **out) {
         return fail(FMX_EUNSUPPORTED, "no batched kernel for m = %d", ps[0].m);
     }
     int pt = 0, ph = 0;
-    b->pol_ok = fmx::fused2d_pol_batch_geometry(b->m, 0, false, &pt, &ph, &b->pwidth, &b->psmem, &b->pbps) == 0;
+    b->pol_ok = fmx::fused2d_pol_batch_geometry(b->m, 0, false, &pt, &ph, &b->pwidth, &b->psmem, &b->pbps,
+                                                &b->pwidth_n, &b->pnbytes) == 0;
     *out = b;
     return FMX_OK;
 }
@@ -1762,6 +1787,7 @@ size_t fmx_batch_workspace_bytes(const fmx_batch *b) {
     size_t items = 0;
     int width = b->width > 0 ? b->width : 1;
     if (b->pol_ok && b->pwidth > 0 && b->pwidth < width) width = b->pwidth;
+    if (b->pol_ok && b->pwidth_n > 0 && b->pwidth_n < width) width = b->pwidth_n;
     for (int i = 0; i < b->n; ++i) {
         const size_t ns = ((size_t)b->p[i].n[0] + width - 1) / width;
         items += ns * (((size_t)b->p[i].n[1] + 31) / 32 + 1);
@@ -1797,7 +1823,7 @@ fmx_status fmx_batch_bind(fmx_batch *b, const fmx_buffers *bufs, void *work, siz
     {
         int pt = 0, ph = 0;
         b->pol_ok = fmx::fused2d_pol_batch_geometry(b->m, b->hj ? b->passes : 0, b->hj, &pt, &ph, &b->pwidth,
-                                                    &b->psmem, &b->pbps) == 0;
+                                                    &b->psmem, &b->pbps, &b->pwidth_n, &b->pnbytes) == 0;
     }
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1864,6 +1890,31 @@ fmx_status fmx_batch_set_rows(fmx_batch *b, int rows) {
     return s;
 }
 
+fmx_status fmx_batch_set_tiles(fmx_batch *b, int narrow_policy) {
+    if (!b || narrow_policy < 0 || narrow_policy > 2) return fail(FMX_EINVAL, "bad arguments");
+    if (!b->bound) return fail(FMX_ESTATE, "batch not bound");
+    b->narrow_policy = narrow_policy;
+    const fmx_status s = batch_build(b);
+    if (s != FMX_OK) b->bound = false;
+    return s;
+}
+
+fmx_status fmx_batch_tiles(const fmx_batch *b, int *wide, int *narrow, int *single, int *rows, int *narrow_policy) {
+    if (!b) return fail(FMX_EINVAL, "NULL batch");
+    if (!b->bound) return fail(FMX_ESTATE, "batch not bound");
+    if (wide) *wide = b->nwide;
+    if (narrow) *narrow = b->nnarrow;
+    if (single) *single = b->nitems - b->npol;
+    if (rows) *rows = b->rows_policy;
+    if (narrow_policy) *narrow_policy = b->narrow_policy;
+    return FMX_OK;
+}
+
+int fmx_batch_grid_width(const fmx_batch *b, int i) {
+    if (!b || !b->bound || i < 0 || i >= b->n) return -1;
+    return b->grids[i].W;
+}
+
 fmx_status fmx_batch_step(fmx_batch *b, int nsteps) {
     if (!b) return fail(FMX_EINVAL, "NULL batch");
     if (!b->bound) return fail(FMX_ESTATE, "batch not bound");
@@ -1890,34 +1941,74 @@ fmx_status fmx_batch_step(fmx_batch *b, int nsteps) {
     return FMX_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// tuner choices by batch signature (m, passes, current, every grid's size):
+// a later batch of the same grids reuses them without trial steps
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<int, int>> g_tune_cache;
+
+std::string batch_signature(const fmx_batch *b) {
+    std::string k = std::to_string(b->m) + "/" + std::to_string(b->passes) + "/" + std::to_string((int)b->hj);
+    for (int i = 0; i < b->n; ++i) k += ":" + std::to_string(b->p[i].n[0]) + "x" + std::to_string(b->p[i].n[1]);
+    return k;
+}
+}  // namespace
+
+extern "C" {
+
 fmx_status fmx_batch_tune(fmx_batch *b, int trial_steps, int *chosen) {
     if (!b || trial_steps < 2) return fail(FMX_EINVAL, "bad arguments");
     if (!b->bound) return fail(FMX_ESTATE, "batch not bound");
+    const std::string key = batch_signature(b);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            b->narrow_policy = it->second.second;
+            if (chosen) *chosen = it->second.first;
+            return fmx_batch_set_rows(b, it->second.first);
+        }
+    }
+    // tile rule (narrow tiles where they compute fewer columns, or wide tiles
+    // only) x rows per segment (automatic, then fixed heights)
+    const int rule[] = {1, 0};
     const int cand[] = {0, 1024, 512, 256, 128, 64, 32};
     float best = 1e30f;
-    int best_rows = 0;
+    int best_rows = 0, best_rule = 1;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return fail(FMX_ECUDA, "cudaEventCreate");
     fmx_status s = FMX_OK;
-    for (int rows : cand) {
-        if ((s = fmx_batch_set_rows(b, rows)) != FMX_OK) break;
-        if ((s = fmx_batch_step(b, 2)) != FMX_OK) break;  // capture + warm
-        cudaEventRecord(e0, b->stream);
-        if ((s = fmx_batch_step(b, trial_steps / 2 * 2)) != FMX_OK) break;
-        cudaEventRecord(e1, b->stream);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-            best = ms;
-            best_rows = rows;
+    for (int nr : rule) {
+        b->narrow_policy = nr;
+        for (int rows : cand) {
+            if ((s = fmx_batch_set_rows(b, rows)) != FMX_OK) break;
+            if ((s = fmx_batch_step(b, 2)) != FMX_OK) break;  // capture + warm
+            cudaEventRecord(e0, b->stream);
+            if ((s = fmx_batch_step(b, trial_steps / 2 * 2)) != FMX_OK) break;
+            cudaEventRecord(e1, b->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_rows = rows;
+                best_rule = nr;
+            }
         }
+        if (s != FMX_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (s != FMX_OK) return s;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = {best_rows, best_rule};
+    }
     if (chosen) *chosen = best_rows;
+    b->narrow_policy = best_rule;
     return fmx_batch_set_rows(b, best_rows);
 }
 

@@ -87,12 +87,14 @@ int fused2d_batch_geometry(int m, int passes, bool hj, int *threads, int *halo, 
                            int *blocks_per_sm);
 int launch_fused2d_batch(int m, int passes, bool hj, const BatchGrid *grids, const BatchItem *items, int nitems,
                          int parity, int nblocks, size_t smem, cudaStream_t s);
-// The same on the polarisation-split column-pair kernels (fused2d_pol.cu) for
-// grids of the unlumped scheme: one launch runs the TE and the TM half of
-// every item.
+// The same on the polarisation-split column-pair kernels (fused2d_pol_batch.cu)
+// for grids of the unlumped scheme: one launch runs the TE and the TM half of
+// every item.  Items are wide tiles (the whole CTA, `width` columns written)
+// followed by narrow tiles (half a CTA each, `width_narrow` columns, two per
+// CTA, `narrow_bytes` of shared memory each).
 int fused2d_pol_batch_geometry(int m, int passes, bool hj, int *threads, int *halo, int *width, size_t *smem,
-                               int *blocks_per_sm);
-int launch_fused2d_pol_batch(int m, int passes, bool hj, const BatchGrid *grids, const BatchItem *items, int nitems,
-                             int parity, int nblocks, size_t smem, cudaStream_t s);
+                               int *blocks_per_sm, int *width_narrow, size_t *narrow_bytes);
+int launch_fused2d_pol_batch(int m, int passes, bool hj, const BatchGrid *grids, const BatchItem *items, int nwide,
+                             int nnarrow, int parity, int nblocks, size_t smem, size_t narrow_bytes, cudaStream_t s);
 
 }  // namespace fmx

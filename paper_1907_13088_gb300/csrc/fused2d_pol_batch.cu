@@ -28,16 +28,27 @@ __global__ void __launch_bounds__(NT, 3)
     else pol_tile<POL, M, P, HJ, NT, true>(a, g, c, W, L, strip, seg, sm);
 }
 
-// Batched step on the polarisation kernels: a persistent loop over 2 x nitems
-// virtual items, item v the TE (v even) or TM (v odd) half of tile items[v/2]
-// of its grid; one launch per step covers both halves of every tile.
+// Batched step on the polarisation kernels: a persistent loop over tasks.
+// Task v < 2 nwide is the TE (v even) or TM (v odd) half of the wide tile
+// items[v/2] (the whole CTA, NT column pairs); the tasks after them take the
+// narrow tiles (NT/2 column pairs) two at a time, one per half of the CTA,
+// both in the same polarisation.  One launch per step covers both halves of
+// every tile.
 template <int M, int P, bool HJ, int NT>
 __global__ void __launch_bounds__(NT, 3)
-    k_pol2d_batch(const BatchGrid *__restrict__ grids, const BatchItem *__restrict__ items, int nitems, int parity) {
+    k_pol2d_batch(const BatchGrid *__restrict__ grids, const BatchItem *__restrict__ items, int nwide, int nnarrow,
+                  int parity, int narrow_floats) {
     extern __shared__ __align__(16) unsigned char smraw[];
     float *sm = reinterpret_cast<float *>(smraw);
-    for (int v = blockIdx.x; v < 2 * nitems; v += gridDim.x) {
-        const BatchItem w = items[v >> 1];
+    constexpr int NH = NT / 2;
+    const int npair = (nnarrow + 1) / 2;
+    for (int v = blockIdx.x; v < 2 * (nwide + npair); v += gridDim.x) {
+        __syncthreads();  // both halves are done with the previous task's shared memory
+        const bool narrow = v >= 2 * nwide;
+        const int half = narrow ? (int)threadIdx.x / NH : 0;
+        const int it = narrow ? nwide + 2 * ((v - 2 * nwide) >> 1) + half : v >> 1;
+        if (narrow && it >= nwide + nnarrow) continue;  // the odd last narrow tile has one half idle
+        const BatchItem w = items[it];
         const BatchGrid &G = grids[w.grid];
         Fused2dArgs<float> a{};
 #pragma unroll
@@ -52,14 +63,27 @@ __global__ void __launch_bounds__(NT, 3)
         a.passes = P;
         const Geo g = G.g;
         const Coef2 c = coef2_of(G.c, P);
-        const int xs = w.strip * G.W - PolGeom<M, P, HJ>::HC;
-        const bool seam = (g.nx & 1) && !(xs >= 0 && xs + 2 * NT <= g.nx);
-        if (!seam) {
-            if (v & 1) pol_tile<TM, M, P, HJ, NT>(a, g, c, G.W, G.L, w.strip, w.seg, sm);
-            else pol_tile<TE, M, P, HJ, NT>(a, g, c, G.W, G.L, w.strip, w.seg, sm);
+        if (!narrow) {
+            const int xs = w.strip * G.W - PolGeom<M, P, HJ>::HC;
+            const bool seam = (g.nx & 1) && !(xs >= 0 && xs + 2 * NT <= g.nx);
+            if (!seam) {
+                if (v & 1) pol_tile<TM, M, P, HJ, NT>(a, g, c, G.W, G.L, w.strip, w.seg, sm);
+                else pol_tile<TE, M, P, HJ, NT>(a, g, c, G.W, G.L, w.strip, w.seg, sm);
+            } else {
+                if (v & 1) pol_tile<TM, M, P, HJ, NT, true>(a, g, c, G.W, G.L, w.strip, w.seg, sm);
+                else pol_tile<TE, M, P, HJ, NT, true>(a, g, c, G.W, G.L, w.strip, w.seg, sm);
+            }
         } else {
-            if (v & 1) pol_tile<TM, M, P, HJ, NT, true>(a, g, c, G.W, G.L, w.strip, w.seg, sm);
-            else pol_tile<TE, M, P, HJ, NT, true>(a, g, c, G.W, G.L, w.strip, w.seg, sm);
+            float *smh = sm + half * narrow_floats;
+            const int xs = w.strip * G.W - PolGeom<M, P, HJ>::HC;
+            const bool seam = (g.nx & 1) && !(xs >= 0 && xs + 2 * NH <= g.nx);
+            if (!seam) {
+                if (v & 1) pol_tile<TM, M, P, HJ, NH, false, true>(a, g, c, G.W, G.L, w.strip, w.seg, smh, half);
+                else pol_tile<TE, M, P, HJ, NH, false, true>(a, g, c, G.W, G.L, w.strip, w.seg, smh, half);
+            } else {
+                if (v & 1) pol_tile<TM, M, P, HJ, NH, true, true>(a, g, c, G.W, G.L, w.strip, w.seg, smh, half);
+                else pol_tile<TE, M, P, HJ, NH, true, true>(a, g, c, G.W, G.L, w.strip, w.seg, smh, half);
+            }
         }
     }
 }
@@ -100,17 +124,23 @@ FMX_POL_ODD_M(4)
 }  // namespace pol2d
 
 int fused2d_pol_batch_geometry(int m, int passes, bool hj, int *threads, int *halo, int *width, size_t *smem,
-                               int *blocks_per_sm) {
+                               int *blocks_per_sm, int *width_narrow, size_t *narrow_bytes) {
     int rc = -1;
 #define FMX_PBG(MM, PP, HH)                                                                                    \
     if (m == MM && passes == PP && hj == HH) {                                                               \
         using Gm = PolGeom<MM, PP, HH>;                                                                     \
         constexpr int NT = 128;                                                                             \
         const size_t te = pol2d::smem_bytes<TE, MM, PP, HH>(), tm = pol2d::smem_bytes<TM, MM, PP, HH>(); \
+        const size_t te2 = pol2d::smem_bytes<TE, MM, PP, HH, NT / 2>(),                                  \
+                     tm2 = pol2d::smem_bytes<TM, MM, PP, HH, NT / 2>();                                  \
+        const size_t nb2 = ((te2 > tm2 ? te2 : tm2) + 15) / 16 * 16;                                        \
         *threads = NT;                                                                                      \
         *halo = Gm::HC;                                                                                     \
         *width = 2 * NT - 2 * Gm::HC - 2;                                                                   \
+        *width_narrow = NT - 2 * Gm::HC - 2;                                                                \
+        *narrow_bytes = nb2;                                                                                \
         *smem = te > tm ? te : tm;                                                                          \
+        if (2 * nb2 > *smem) *smem = 2 * nb2;                                                              \
         auto k = k_pol2d_batch<MM, PP, HH, NT>;                                                             \
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);                   \
         int nb = 0;                                                                                         \
@@ -123,12 +153,13 @@ int fused2d_pol_batch_geometry(int m, int passes, bool hj, int *threads, int *ha
     return rc;
 }
 
-int launch_fused2d_pol_batch(int m, int passes, bool hj, const BatchGrid *grids, const BatchItem *items, int nitems,
-                             int parity, int nblocks, size_t smem, cudaStream_t s) {
-#define FMX_PBL(MM, PP, HH)                                                                       \
-    if (m == MM && passes == PP && hj == HH) {                                                   \
-        k_pol2d_batch<MM, PP, HH, 128><<<nblocks, 128, smem, s>>>(grids, items, nitems, parity); \
-        return 1;                                                                               \
+int launch_fused2d_pol_batch(int m, int passes, bool hj, const BatchGrid *grids, const BatchItem *items, int nwide,
+                             int nnarrow, int parity, int nblocks, size_t smem, size_t narrow_bytes, cudaStream_t s) {
+    const int nf = (int)(narrow_bytes / sizeof(float));
+#define FMX_PBL(MM, PP, HH)                                                                                    \
+    if (m == MM && passes == PP && hj == HH) {                                                               \
+        k_pol2d_batch<MM, PP, HH, 128><<<nblocks, 128, smem, s>>>(grids, items, nwide, nnarrow, parity, nf); \
+        return 1;                                                                                            \
     }
     FMX_PBL(4, 0, false) FMX_PBL(4, 3, true) FMX_PBL(2, 0, false) FMX_PBL(1, 0, false) FMX_PBL(0, 0, false)
 #undef FMX_PBL

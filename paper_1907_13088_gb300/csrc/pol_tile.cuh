@@ -81,10 +81,13 @@ struct PolSmem {
 };
 
 // One tile: strip `strip` (W columns written) and segment `seg` (L rows) of a
-// grid, in the shared memory `sm` (PolSmem layout).
-template <int POL, int M, int P, bool HJ, int NT, bool SEAM = false>
+// grid, in the shared memory `sm` (PolSmem layout).  HALF: the tile is run by
+// one half of the CTA (threads half * NT .. half * NT + NT - 1), which
+// synchronises on its own named barrier 1 + half, so that a CTA can carry
+// two independent narrow tiles; otherwise the whole CTA runs it.
+template <int POL, int M, int P, bool HJ, int NT, bool SEAM = false, bool HALF = false>
 __device__ __forceinline__ void pol_tile(const Fused2dArgs<float> &a, const Geo &g, const Coef2 &c, int W, int L,
-                                         int strip, int seg, float *sm) {
+                                         int strip, int seg, float *sm, int half = 0) {
     using G = PolGeom<M, P, HJ>;
     constexpr int HC = G::HC, PADP = G::PADP, TJ = G::TJ;
     constexpr int RP = NT + 2 * PADP;  // pairs (floats of a half row) per smem row
@@ -100,7 +103,11 @@ __device__ __forceinline__ void pol_tile(const Fused2dArgs<float> &a, const Geo 
     float *s_sw = sm + S::SW;
     float *s_e = sm + S::EN;
 
-    const int tid = threadIdx.x;
+    const int tid = HALF ? (int)threadIdx.x - half * NT : (int)threadIdx.x;
+    auto row_barrier = [&]() {
+        if constexpr (HALF) asm volatile("bar.sync %0, %1;" ::"r"(1 + half), "n"(NT) : "memory");
+        else __syncthreads();
+    };
     for (int q = tid; q < S::TOTAL; q += NT) sm[q] = 0.f;
 
     const int x0 = strip * W;
@@ -253,7 +260,7 @@ __device__ __forceinline__ void pol_tile(const Fused2dArgs<float> &a, const Geo 
     constexpr int DRS = NC * 2 * RP;  // floats per dE' ring row
     float *gA = s_dp + b0 * DRS, *gB = s_dp + ((b0 + 4) % D0) * DRS, *gC = s_dp + ((b0 + 8) % D0) * DRS;
 
-    __syncthreads();
+    row_barrier();
 
     for (int rb = r0; rb < r1; rb += 4) {
 #pragma unroll
@@ -508,7 +515,7 @@ __device__ __forceinline__ void pol_tile(const Fused2dArgs<float> &a, const Geo 
                     put(s_ay + ((u + 1) & 1) * 2 * RP, fma(c6(), fma(byw[1], m2(), add(byw[0], byw[2])), byw[1]));
                 }
             }
-            __syncthreads();
+            row_barrier();
         }
         b0 += 4;
         if (b0 >= D0) b0 -= D0;
@@ -534,10 +541,10 @@ __host__ __device__ inline Coef2 coef2_of(const Coef<float> &c, int passes) {
     return k;
 }
 
-// dynamic shared memory of a tile
-template <int POL, int M, int P, bool HJ>
+// dynamic shared memory of a tile of NT column pairs
+template <int POL, int M, int P, bool HJ, int NT = 128>
 inline size_t smem_bytes() {
-    return (size_t)PolSmem<POL, M, P, HJ, 128 + 2 * PolGeom<M, P, HJ>::PADP>::TOTAL * sizeof(float);
+    return (size_t)PolSmem<POL, M, P, HJ, NT + 2 * PolGeom<M, P, HJ>::PADP>::TOTAL * sizeof(float);
 }
 
 // grids with odd n_x (fused2d_pol_batch.cu): the strips that cross the

@@ -120,6 +120,9 @@ def _load():
         "fmx_batch_get_fields": (ctypes.c_int, [G, ctypes.c_int, ctypes.c_uint, vpp, ctypes.c_int]),
         "fmx_batch_set_rows": (ctypes.c_int, [G, ctypes.c_int]),
         "fmx_batch_tune": (ctypes.c_int, [G, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+        "fmx_batch_set_tiles": (ctypes.c_int, [G, ctypes.c_int]),
+        "fmx_batch_grid_width": (ctypes.c_int, [G, ctypes.c_int]),
+        "fmx_batch_tiles": (ctypes.c_int, [G] + [ctypes.POINTER(ctypes.c_int)] * 5),
         "fmx_batch_step": (ctypes.c_int, [G, ctypes.c_int]),
         "fmx_batch_items": (ctypes.c_int, [G]),
         "fmx_batch_launch_count": (ctypes.c_int64, [G]),
@@ -181,6 +184,9 @@ fmx_batch_get_fields = _lib.fmx_batch_get_fields
 fmx_batch_set_rows = _lib.fmx_batch_set_rows
 fmx_batch_tune = _lib.fmx_batch_tune
 fmx_batch_step = _lib.fmx_batch_step
+fmx_batch_set_tiles = _lib.fmx_batch_set_tiles
+fmx_batch_tiles = _lib.fmx_batch_tiles
+fmx_batch_grid_width = _lib.fmx_batch_grid_width
 fmx_batch_items = _lib.fmx_batch_items
 fmx_batch_launch_count = _lib.fmx_batch_launch_count
 fmx_batch_destroy = _lib.fmx_batch_destroy
@@ -534,6 +540,18 @@ class Batch:
 
     def set_rows(self, rows):
         check(fmx_batch_set_rows(self.handle, int(rows)), "fmx_batch_set_rows")
+
+    def set_tiles(self, narrow_rule):
+        check(fmx_batch_set_tiles(self.handle, int(narrow_rule)), "fmx_batch_set_tiles")
+
+    def tiles(self) -> dict:
+        v = [ctypes.c_int(0) for _ in range(5)]
+        check(fmx_batch_tiles(self.handle, *[ctypes.byref(x) for x in v]), "fmx_batch_tiles")
+        return dict(zip(("wide", "narrow", "single", "rows", "narrow_rule"), (x.value for x in v)))
+
+    def grid_width(self, i) -> int:
+        """Columns one tile of grid i writes (fmx_batch_grid_width)."""
+        return int(fmx_batch_grid_width(self.handle, int(i)))
 
     def tune(self, trial_steps=20) -> int:
         chosen = ctypes.c_int(0)

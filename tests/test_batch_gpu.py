@@ -143,3 +143,48 @@ def test_batch_failed_rebuild_unbinds(fmx):
     assert ei.value.status == fmx.FMX_ESTATE
     assert b.launches == n0
     b.close()
+
+
+@pytest.mark.parametrize("rule", [0, 1, 2])
+@pytest.mark.parametrize("with_j", [False, True])
+def test_batch_tile_rules_match_oracle(fmx, rule, with_j):
+    """Wide tiles only (0), narrow tiles where they compute fewer columns (1)
+    and narrow tiles everywhere (2; two independent tiles per CTA on named
+    barriers, including the seam tiles of odd n_x): the same results, every
+    grid against the oracle, with and without a filtered current."""
+    kw = dict(m=4, filter_passes=3, with_current=True) if with_j else dict(m=4)
+    b = fmx.Batch(SHAPES, COURANT, **kw)
+    b.set_tiles(rule)
+    t = b.tiles()
+    assert t["narrow_rule"] == rule
+    if rule == 0:
+        assert t["narrow"] == 0
+    if rule == 2:
+        assert t["wide"] == 0 and t["narrow"] > 0
+    inputs = [_fields(sh, 1907060 + i) for i, sh in enumerate(SHAPES)]
+    currents = [synth.solenoidal_current(sh, 1907070 + i, width=4.0, rms=1e-2) for i, sh in enumerate(SHAPES)]
+    for i, (E, B) in enumerate(inputs):
+        b.set_fields(i, E, B)
+        if with_j:
+            b.set_current(i, currents[i])
+    nsteps = 5
+    b.step(nsteps)
+    for i, (sh, cf) in enumerate(zip(SHAPES, COURANT)):
+        Eg, Bg = b.get_fields(i)
+        E, B = inputs[i]
+        J = currents[i].astype(np.float64) if with_j else None
+        Eo, Bo, rc, _ = core.step(core.Params(shape=sh, courant=cf, m=4, filter_passes=3 if with_j else 0,
+                                              coef_f32=True), E.astype(np.float64), B.astype(np.float64), J, nsteps)
+        assert_parity(Eg, Bg, Eo, Bo, TOL32, f"rule {rule} grid {i} {sh}")
+
+
+def test_batch_tune_caches_its_choice(fmx):
+    """A second batch of the same grids takes the tuned choice from the
+    process cache, without trial steps (its step counter does not move)."""
+    b = fmx.Batch(SHAPES, COURANT, m=4)
+    rows = b.tune(trial_steps=4)
+    first = b.tiles()
+    b2 = fmx.Batch(SHAPES, COURANT, m=4)
+    rows2 = b2.tune(trial_steps=4)
+    assert rows2 == rows and b2.tiles()["narrow_rule"] == first["narrow_rule"]
+    assert b2.launches == 0, "the cached choice needs no trial steps"
