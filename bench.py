@@ -697,6 +697,8 @@ def run_res64(args):
             torch.cuda.synchronize()
             nl = g.launches - l0
             reps.append((ev0.elapsed_time(ev1) * 1e-3, g.diagnostics()["total_sweeps"] - s0, nl))
+        if engine == fmx.FMX_ENGINE_RESIDENT:
+            clusters = g.get_option(fmx.FMX_OPT_RESIDENT_CLUSTERS)
         out[name] = reps[-1]
         g.close()
     secs, sweeps, launches = out["resident"]
@@ -709,7 +711,7 @@ def run_res64(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "2D periodic 64x64 FP64, 8 TM plane waves |n|<=8 (seed 1907001), no current, "
                                "no filter, residual 1e-13 every step (Algorithm 1), 200 steps, dt=0.5 dt_CFL",
-                   "engine": "resident (one thread-block cluster, all steps in one launch)",
+                   "engine": f"resident (all steps in one launch of {clusters} thread-block cluster(s))",
                    "sweeps_per_step": round(sweeps / nsteps, 2),
                    "variants": ctx,
                    "timing": "CUDA events on the grid's stream around the 200 steps (the call reads the "

@@ -73,6 +73,13 @@ enum { FMX_F32 = 0, FMX_F64 = 1 };                        /* storage and sweep p
  * the staged engine. */
 enum { FMX_ITER_FIXED = 0, FMX_ITER_RESIDUAL = 1, FMX_ITER_CHEB_FIXED = 2, FMX_ITER_CHEB_RESIDUAL = 3 };
 enum { FMX_FILTER_NONE = 0, FMX_FILTER_CURRENT = 1, FMX_FILTER_FIELDS = 2 };
+/* Engines: STAGED, one kernel per stage (every mode and dimension); FUSED, the
+ * 2D fixed-m step in one or two kernels per step; RESIDENT, all the steps of
+ * an fmx_step call, with Algorithm 1's sweeps (fixed m or to the residual) in
+ * one launch of one or more thread-block clusters, for grids of at most
+ * 262144 cells (no Chebyshev modes, no field filter); AUTO takes FUSED where
+ * it applies, RESIDENT for residual mode on grids of at most 16384 FP64 or
+ * 65536 FP32 cells, else STAGED. */
 enum { FMX_ENGINE_AUTO = 0, FMX_ENGINE_STAGED = 1, FMX_ENGINE_FUSED = 2, FMX_ENGINE_RESIDENT = 3 };
 enum { FMX_HOST = 0, FMX_DEVICE = 1 };                    /* where a copy source/target lives */
 
@@ -511,9 +518,26 @@ fmx_status fmx_step_static(const fmx_params *p, void *const *E, void *const *B, 
  *     of sweeps in one pass, the intermediate sweep kept on chip on a tile
  *     grown by one cell; an odd last sweep takes a pass of its own).  Same
  *     results to FP32 rounding.  Default 1.
- * fmx_set_option returns FMX_EINVAL for an unknown option or value;
- * fmx_get_option returns the value, or -1 (unknown option or NULL grid). */
-enum { FMX_OPT_SWEEPS_PER_PASS = 1 };
+ *   FMX_OPT_WAIT_LIMIT_US: how long (microseconds of SM clock at the
+ *     device's rated clock) a resident launch over several clusters waits at
+ *     its grid barrier before it gives up: the launch then stops between two
+ *     phases, the call returns FMX_ETIMEOUT and the fields hold a partly
+ *     advanced state.  Default 1000000 (1 s).
+ *   FMX_OPT_SELFTEST_LOST_ARRIVAL: 1 makes the resident launch's grid barrier
+ *     expect one arrival more than ever comes, so that its first wait runs out
+ *     (a test of the time-out path that faults nothing); 0 (default) is the
+ *     normal barrier.
+ *   FMX_OPT_RESIDENT_CLUSTERS (read only): clusters of the last resident
+ *     launch (0 before the first).
+ * fmx_set_option returns FMX_EINVAL for an unknown or read-only option or a
+ * bad value; fmx_get_option returns the value, or -1 (unknown option or NULL
+ * grid). */
+enum {
+    FMX_OPT_SWEEPS_PER_PASS = 1,
+    FMX_OPT_WAIT_LIMIT_US = 2,
+    FMX_OPT_SELFTEST_LOST_ARRIVAL = 3,
+    FMX_OPT_RESIDENT_CLUSTERS = 4
+};
 fmx_status fmx_set_option(fmx_grid *g, int option, int value);
 int fmx_get_option(const fmx_grid *g, int option);
 

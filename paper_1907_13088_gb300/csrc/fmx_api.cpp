@@ -297,6 +297,11 @@ struct fmx_grid {
     cudaEvent_t ev_in = nullptr, ev_comp = nullptr, ev_out = nullptr;
     // sweeps of Algorithm 1 per z-march pass of the 3D kernels (fmx_set_option)
     int sweeps_per_pass = 1;
+    // resident engine: limit of a wait at its grid barrier, the self-test of
+    // that wait, and the clusters of the last launch
+    long long wait_limit_us = 1000000;
+    int lost_arrival = 0;
+    int last_clusters = 0;
     // Chebyshev modes: the interval holding the eigenvalues of A, and the
     // recurrence's constants
     double cheb_lo = 0.0, cheb_hi = 0.0;
@@ -545,9 +550,12 @@ fmx_status staged_step(fmx_grid *g) {
     return FMX_OK;
 }
 
-// Resident engine: nsteps steps in one cluster launch.  Residual mode reads
-// the solver status back once (synchronising: it reports FMX_ENOCONV and the
-// sweep counts); fixed m stays asynchronous.
+// Resident engine: nsteps steps in one launch (one cluster, or several in a
+// cooperative launch).  The status word is cleared first (arrival count,
+// generation, latched error).  Residual mode, and any launch over several
+// clusters, reads the status back once (synchronising: it reports FMX_ENOCONV,
+// FMX_ETIMEOUT and the sweep counts); fixed m on one cluster stays
+// asynchronous.
 template <typename T>
 fmx_status resident_steps(fmx_grid *g, int nsteps) {
     if (nsteps == 0) return FMX_OK;
@@ -556,22 +564,45 @@ fmx_status resident_steps(fmx_grid *g, int nsteps) {
     const bool resid = g->p.iter_mode == FMX_ITER_RESIDUAL;
     const bool have_j = g->buf.J[0] != nullptr;
     const int jpasses = (have_j && g->p.filter_target == FMX_FILTER_CURRENT) ? g->p.filter_passes : 0;
-    const int n = fmx::launch_resident<T>(g->geo, g->p.dims, c, P, nsteps, resid, g->p.m, g->p.tol * g->p.tol,
-                                          g->p.m_max, jpasses, g->stream);
-    if (n < 0) return cuda_fail(cudaGetLastError(), "resident launch");
-    g->launches += n;
+    int dev = 0, khz = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess || khz <= 0) khz = 2000000;
+    fmx::ResidentWait wait;
+    wait.limit_cycles = (long long)g->wait_limit_us * (long long)khz / 1000;
+    wait.lost_arrival = g->lost_arrival;
+    cudaError_t e = cudaMemsetAsync(g->st, 0, sizeof(fmx::DevStatus), g->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (status)");
+    const int ncl = fmx::launch_resident<T>(g->geo, g->p.dims, c, P, nsteps, resid, g->p.m, g->p.tol * g->p.tol,
+                                            g->p.m_max, jpasses, wait, g->stream);
+    if (ncl < 0) return cuda_fail(cudaGetLastError(), "resident launch");
+    g->launches += 1;
     fmx_status s = check_launch(g, "resident launch");
     if (s != FMX_OK) return s;
-    if (!resid) {
+    g->last_clusters = ncl;
+    if (!resid && ncl == 1 && !wait.lost_arrival) {
         g->last_sweeps = g->p.m;
         g->total_sweeps += (int64_t)g->p.m * nsteps;
         g->steps += nsteps;
         return FMX_OK;
     }
     fmx::DevStatus hs;
-    cudaError_t e = cudaMemcpyAsync(&hs, g->st, sizeof(hs), cudaMemcpyDeviceToHost, g->stream);
+    e = cudaMemcpyAsync(&hs, g->st, sizeof(hs), cudaMemcpyDeviceToHost, g->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return cuda_fail(e, "resident status read-back");
+    if (hs.err) {
+        // a grid-barrier wait ran out: the launch stopped between two phases and
+        // the fields hold a partly advanced state
+        const fmx_status err = (fmx_status)hs.err;
+        cudaMemsetAsync(&g->st->err, 0, sizeof(int), g->stream);
+        return fail(err, "resident launch over %d cluster(s): a wait at the grid barrier ran out after %lld us", ncl,
+                    g->wait_limit_us);
+    }
+    if (!resid) {
+        g->last_sweeps = g->p.m;
+        g->total_sweeps += (int64_t)g->p.m * nsteps;
+        g->steps += nsteps;
+        return FMX_OK;
+    }
     g->last_sweeps = hs.count;
     g->total_sweeps += hs.sweeps_total;
     g->last_resid = hs.nrm2 > 0.0 ? sqrt(hs.r2 / hs.nrm2) : 0.0;
@@ -1382,13 +1413,27 @@ fmx_status fmx_set_option(fmx_grid *g, int option, int value) {
             if (value != 1 && value != 2) return fail(FMX_EINVAL, "sweeps per pass must be 1 or 2 (got %d)", value);
             g->sweeps_per_pass = value;
             return FMX_OK;
+        case FMX_OPT_WAIT_LIMIT_US:
+            if (value < 1) return fail(FMX_EINVAL, "wait limit must be >= 1 us (got %d)", value);
+            g->wait_limit_us = value;
+            return FMX_OK;
+        case FMX_OPT_SELFTEST_LOST_ARRIVAL:
+            if (value != 0 && value != 1) return fail(FMX_EINVAL, "lost-arrival self-test is 0 or 1 (got %d)", value);
+            g->lost_arrival = value;
+            return FMX_OK;
     }
     return fail(FMX_EINVAL, "unknown option %d", option);
 }
 
 int fmx_get_option(const fmx_grid *g, int option) {
     if (!g) return -1;
-    return option == FMX_OPT_SWEEPS_PER_PASS ? g->sweeps_per_pass : -1;
+    switch (option) {
+        case FMX_OPT_SWEEPS_PER_PASS: return g->sweeps_per_pass;
+        case FMX_OPT_WAIT_LIMIT_US: return (int)g->wait_limit_us;
+        case FMX_OPT_SELFTEST_LOST_ARRIVAL: return g->lost_arrival;
+        case FMX_OPT_RESIDENT_CLUSTERS: return g->last_clusters;
+    }
+    return -1;
 }
 
 fmx_status fmx_step_host(fmx_grid *g, const fmx_host_step *io, int count) {

@@ -38,6 +38,11 @@ struct DevStatus {
     double cheb_rho; // Chebyshev mode: rho of the last sweep
     int steps;       // resident engine: steps completed by the last launch
     long long sweeps_total;  // resident engine: sweeps of all those steps
+    // resident engine over several clusters: the grid barrier's arrival count
+    // and generation, and the clusters' residual partials (two alternating sets)
+    unsigned bar_count;
+    unsigned bar_gen;
+    double xpart[2][8];
 };
 
 // Chebyshev acceleration: M = 1 - A has its spectrum in [1 - hi, 1 - lo];
@@ -126,9 +131,20 @@ int launch_march3d_faraday(const Geo &g, const Coef<T> &c, const T *const E[3], 
 // current (once per launch, into P.jf).  Results in P.st (count = sweeps of
 // the last step, steps, sweeps_total, noconv).  Returns 1, or -1 when the
 // launch failed.
+// Returns the clusters launched (one launch), or -1 when the launch failed.
+// wait: the bounded software wait of a launch over several clusters (its
+// limit in SM clock cycles; lost_arrival makes the wait expect one cluster
+// more than exist, so that it must time out: a self-test of that path).
+struct ResidentWait {
+    long long limit_cycles;
+    int lost_arrival;
+};
 template <typename T>
 int launch_resident(const Geo &g, int dims, const Coef<T> &c, const StagedPtrs<T> &P, int nsteps, bool resid, int m,
-                    double tol2, int m_max, int jpasses, cudaStream_t s);
+                    double tol2, int m_max, int jpasses, const ResidentWait &wait, cudaStream_t s);
+// clusters the resident engine launches for a grid of `cells` cells
+template <typename T>
+int resident_clusters(int dims, int64_t cells, bool lost_arrival);
 // CTAs in the cluster the resident kernel launches with (16 where the device
 // runs clusters of 16, else 8)
 template <typename T>

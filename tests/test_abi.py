@@ -110,6 +110,14 @@ def test_validation_codes(fmx):
     assert fmx.fmx_get_option(h, fmx.FMX_OPT_SWEEPS_PER_PASS) == 2
     assert fmx.fmx_set_option(h, fmx.FMX_OPT_SWEEPS_PER_PASS, 3) == fmx.FMX_EINVAL
     assert fmx.fmx_set_option(h, 99, 1) == fmx.FMX_EINVAL and fmx.fmx_get_option(h, 99) == -1
+    assert fmx.fmx_get_option(h, fmx.FMX_OPT_WAIT_LIMIT_US) == 1000000
+    assert fmx.fmx_set_option(h, fmx.FMX_OPT_WAIT_LIMIT_US, 0) == fmx.FMX_EINVAL
+    assert fmx.fmx_set_option(h, fmx.FMX_OPT_WAIT_LIMIT_US, 5000) == fmx.FMX_OK
+    assert fmx.fmx_get_option(h, fmx.FMX_OPT_WAIT_LIMIT_US) == 5000
+    assert fmx.fmx_set_option(h, fmx.FMX_OPT_SELFTEST_LOST_ARRIVAL, 2) == fmx.FMX_EINVAL
+    assert fmx.fmx_get_option(h, fmx.FMX_OPT_SELFTEST_LOST_ARRIVAL) == 0
+    assert fmx.fmx_get_option(h, fmx.FMX_OPT_RESIDENT_CLUSTERS) == 0  # no launch yet
+    assert fmx.fmx_set_option(h, fmx.FMX_OPT_RESIDENT_CLUSTERS, 2) == fmx.FMX_EINVAL  # read only
     fmx.fmx_destroy(h)
     # the FMA-rate measurement refuses bad arguments before any device work
     out = ctypes.c_double(0.0)

@@ -162,3 +162,60 @@ def test_resident_time_profile_takes_staged_kernels(fmx):
         Eg, Bg, _ = g.get_fields()
         out.append((np.asarray(Eg, np.float64), np.asarray(Bg, np.float64)))
     assert_parity(out[0][0], out[0][1], out[1][0], out[1][1], 1e-13, "profile")
+
+
+@pytest.mark.parametrize("n", [64, 128])
+def test_resident_launch_clusters_and_parity_fp64(fmx, n):
+    """FP64 solves above ~4096 cells spread over several clusters in one
+    cooperative launch, synchronised by the bounded grid barrier (128^2: four
+    clusters); 64^2 stays on one.  The result does not depend on how many."""
+    shape = (n, n)
+    po = core.Params(shape=shape, courant=0.5, residual=True, tol=1e-13, m_max=10000)
+    E, B, _ = synth.tm_plane_waves(shape, po.time_step(), seed=1907001)
+    g = fmx.Grid(shape, with_current=False, precision=1, iter_mode=1, tol=1e-13, m_max=10000, courant=0.5,
+                 engine=fmx.FMX_ENGINE_RESIDENT)
+    g.set_fields(E, B)
+    g.step(20)
+    ncl = g.get_option(fmx.FMX_OPT_RESIDENT_CLUSTERS)
+    print("resident clusters", n, ncl)
+    assert ncl == 1 if n == 64 else ncl >= 2
+    Eg, Bg, _ = g.get_fields()
+    Eo, Bo, rc, st = core.step(po, E, B, None, 20)
+    assert_parity(np.asarray(Eg, np.float64), np.asarray(Bg, np.float64), Eo, Bo, TOL64, f"{ncl} clusters")
+    assert g.diagnostics()["total_sweeps"] == st["total_sweeps"]
+
+
+@pytest.mark.parametrize("prec,iter_mode", [(1, 1), (0, 0)])
+def test_resident_grid_wait_times_out_and_the_context_survives(fmx, prec, iter_mode):
+    """The bounded wait of the grid barrier: with one arrival that never comes
+    (the self-test option) the first wait runs out after its limit, the call
+    returns FMX_ETIMEOUT, and the same grid then steps normally (the
+    context is intact) and matches the staged engine."""
+    import time
+    shape = (48, 40)
+    dt = np.float64 if prec == 1 else np.float32
+    E, B, J = _inputs(shape, 9, dt)
+    kw = dict(precision=prec, iter_mode=iter_mode, courant=0.6, filter_passes=1)
+    if iter_mode == 1:
+        kw.update(tol=1e-12, m_max=5000)
+    else:
+        kw.update(m=4)
+    g = fmx.Grid(shape, with_current=True, engine=fmx.FMX_ENGINE_RESIDENT, **kw)
+    g.set_fields(E, B)
+    g.set_current(J)
+    g.set_option(fmx.FMX_OPT_WAIT_LIMIT_US, 20000)
+    g.set_option(fmx.FMX_OPT_SELFTEST_LOST_ARRIVAL, 1)
+    t0 = time.perf_counter()
+    with pytest.raises(fmx.FmxError) as ei:
+        g.step(3)
+    waited = time.perf_counter() - t0
+    assert ei.value.status == fmx.FMX_ETIMEOUT
+    assert waited < 5.0, waited  # a 20 ms limit, not a hang
+    g.set_option(fmx.FMX_OPT_SELFTEST_LOST_ARRIVAL, 0)
+    g.set_fields(E, B)
+    g.step(3)
+    g.sync()
+    Er, Br, _ = g.get_fields()
+    Es, Bs, _ = _run(fmx, shape, E, B, J, 3, engine=fmx.FMX_ENGINE_STAGED, **kw)
+    assert_parity(np.asarray(Er, np.float64), np.asarray(Br, np.float64), Es, Bs,
+                  1e-13 if prec == 1 else 1e-6, "after a time-out")
