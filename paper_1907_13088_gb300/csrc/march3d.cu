@@ -9,8 +9,12 @@
 // k-1..k+1 are read while planes k+2..k+RS-2 are on their way (RS ring
 // slots), and the sweep's dE' of the thread's own cell rides in a second ring
 // of the same depth.  One __syncthreads per plane; the slot refilled after it
-// was last read in the previous plane's iteration.  The stencil arithmetic is
-// the staged engine's (stencil.cuh), read through a ring accessor.
+// was last read in the previous plane's iteration.  The stencil arithmetic of
+// these one-column kernels (FP64, odd n_x) is the staged engine's
+// (stencil.cuh), read through a ring accessor.  The FP32 column-pair kernels
+// further down factor the A operator and the averaged curl into in-plane
+// stencils and 3-point combinations along z, so that they read one plane per
+// iteration and carry the z-combinations in registers.
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -255,6 +259,7 @@ using pair2::f2;
 constexpr int TXP = 32, TX2 = 2 * TXP;              // threads along x, columns of the tile
 constexpr int RW2 = TX2 + 4, PL2 = RW2 * RH;         // smem row and plane (one component)
 constexpr int NPC = TXP * RH, NCP2 = NPC + 2 * RH;  // pair copies and halo copies per plane
+constexpr int SWEEP_RS = 8;  // ring slots of the pair sweep: one plane read, seven in flight
 
 struct Coef3P {
     f2 ax, ay, az, ayz, azx, axy, byz, bzx, bxy, c6, kx, ky, kz, q;
@@ -311,11 +316,16 @@ __device__ __forceinline__ f2 apply_a2(const F &V, const Coef3P &c) {
     return r;
 }
 
-// a thread's (at most two) copy items of a component plane
+// a thread's (at most two) copy items of a component plane, and the plane the
+// z-march copies next: its index unwrapped (which picks the ring slot) and
+// the element offset of the plane wrapped periodically, advanced one plane
+// per copy so that no plane index is divided by n_z on the way
 struct PairCopies {
     int s[2], o[2];  // smem index within a component plane (-1: none), global in-plane offset
     bool w[2];       // column pair (8 bytes) or halo column (4 bytes)
-    __device__ __forceinline__ void init(const Geo &g, int x0, int y0) {
+    int ku;          // next plane, unwrapped
+    int64_t off;     // element offset of that plane wrapped into [0, n_z)
+    __device__ __forceinline__ void init(const Geo &g, int x0, int y0, int k0) {
         const int tid = threadIdx.y * TXP + threadIdx.x;
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
@@ -339,33 +349,107 @@ struct PairCopies {
                 o[r] = y * (int)g.pitch + x;
             }
         }
+        ku = k0;
+        off = (int64_t)wrapm(k0, g.nz) * g.plane;
     }
+    // copies plane ku of the N components into ring slot ku mod RS, then
+    // moves on to the next plane
     template <int RS, int N = 3>
-    __device__ __forceinline__ void issue(float *ring, const float *const src[N], const Geo &g, int k) const {
-        const int64_t base = (int64_t)wrapm(k, g.nz) * g.plane;
-        const int slot = k & (RS - 1);
+    __device__ __forceinline__ void issue_next(float *ring, const float *const src[N], const Geo &g) {
+        float *slot = ring + (ku & (RS - 1)) * N * PL2;
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             if (s[r] < 0) continue;
+            const int64_t go = off + o[r];
 #pragma unroll
             for (int c = 0; c < N; ++c) {
-                float *dst = ring + (slot * N + c) * PL2 + s[r];
-                const float *sp = src[c] + base + o[r];
+                float *dst = slot + c * PL2 + s[r];
+                const float *sp = src[c] + go;
                 if (w[r]) cp_async_pair(dst, sp);
                 else cp_async_el(dst, sp);
             }
         }
+        ++ku;
+        off += g.plane;
+        if (off == (int64_t)g.nz * g.plane) off = 0;
     }
 };
 
-// out = dEp + A in, or with UPD: E = E + dEp + A in (the last sweep and the
-// update of the step in one pass; E in place)
-template <bool UPD>
-__global__ void __launch_bounds__(NTH, 2) k3_sweep2(Geo g, Coef3P c, const float *p0, const float *p1,
-                                                   const float *p2, const float *i0, const float *i1, const float *i2,
-                                                   float *o0, float *o1, float *o2) {
+// The A operator factored for a z-march.  Operators along different axes
+// commute, so every element of A (Eqs. matrixA_1st..matrixA_last, 3D) is an
+// in-plane (x, y) stencil of one z-plane followed by a 3-point combination
+// along z:
+//   (A dE)_x(k) = a_y P_k + a_z Dzz Ex + a_yz Dzz P + b_xy (G_k + c6 Dzz G) + b_zx (N_k - N_(k-1)),
+//   (A dE)_y(k) = a_x Q_k + a_z Dzz Ey + a_zx Dzz Q + b_xy (G'_k + c6 Dzz G') + b_yz (N'_k - N'_(k-1)),
+//   (A dE)_z(k) = T_k + H_(k+1) - H_k,
+// with Dzz f = f_(k+1) - 2 f_k + f_(k-1) and the in-plane fields
+//   P = Dbar_yy Ex,  G = Dbar_x(fwd) Dbar_y(bwd) Ey,  N = Dbar_x(fwd) (Ez + c6 Dbar_yy Ez),
+//   Q = Dbar_xx Ey,  G' = Dbar_y(fwd) Dbar_x(bwd) Ex,  N' = Dbar_y(fwd) (Ez + c6 Dbar_xx Ez),
+//   T = (a_x Dbar_xx + a_y Dbar_yy + a_xy Dbar_xx Dbar_yy) Ez,
+//   H = b_zx Dbar_x(bwd) (Ex + c6 Dbar_yy Ex) + b_yz Dbar_y(bwd) (Ey + c6 Dbar_xx Ey).
+// Plane j of the sweep's input therefore reaches outputs j-1, j and j+1
+// through the combinations below, computed once from plane j alone (21
+// shared-memory loads per column pair against 51 for the 27-point form).
+struct PlaneTerms {
+    f2 x1, x0, xl;  // x: to outputs j-1 and j+1 (x1), to j (x0), to j+1 (xl = x1 - b_zx N)
+    f2 y1, y0, yl;  // y: the same with G', N', Q
+    f2 zh, zt;      // z: H to output j-1, T - H to output j
+};
+
+template <typename F>
+__device__ __forceinline__ PlaneTerms plane_terms(const F &V, const Coef3P &c, f2 bxy6) {
     using namespace pair2;
-    constexpr int RS = RingDepth<float>::RS, LA = RingDepth<float>::LA;
+    auto d2 = [](f2 p, f2 o, f2 m) { return fma(o, m2(), add(p, m)); };  // p - 2 o + m
+    auto sub = [](f2 a, f2 b) { return fma(b, m1(), a); };
+    // Ex at columns x-1, x and rows y-1, y, y+1
+    const f2 ex_m = V(0, 0, -1), ex_0 = V(0, 0, 0), ex_p = V(0, 0, 1);
+    const f2 exl_m = V(0, -1, -1), exl_0 = V(0, -1, 0), exl_p = V(0, -1, 1);
+    // Ey at columns x-1, x, x+1 and rows y-1, y
+    const f2 ey_m = V(1, 0, -1), ey_0 = V(1, 0, 0);
+    const f2 eyl_m = V(1, -1, -1), eyl_0 = V(1, -1, 0), eyr_m = V(1, 1, -1), eyr_0 = V(1, 1, 0);
+    // Ez at columns x-1..x+1 and rows y-1..y+1: ez[dy + 1][dx + 1]
+    f2 ez[3][3];
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) ez[dy + 1][dx + 1] = V(2, dx, dy);
+    const f2 P = d2(ex_p, ex_0, ex_m), Pl = d2(exl_p, exl_0, exl_m);  // Dbar_yy Ex at x, x-1
+    const f2 Q = d2(eyr_0, ey_0, eyl_0), Qm = d2(eyr_m, ey_m, eyl_m);  // Dbar_xx Ey at y, y-1
+    const f2 G = sub(sub(eyr_0, ey_0), sub(eyr_m, ey_m));
+    const f2 Gp = sub(sub(ex_p, exl_p), sub(ex_0, exl_0));
+    const f2 dxz_m = d2(ez[0][2], ez[0][1], ez[0][0]), dxz_0 = d2(ez[1][2], ez[1][1], ez[1][0]),
+             dxz_p = d2(ez[2][2], ez[2][1], ez[2][0]);  // Dbar_xx Ez at y-1, y, y+1
+    const f2 dyz_0 = d2(ez[2][1], ez[1][1], ez[0][1]), dyz_r = d2(ez[2][2], ez[1][2], ez[0][2]);  // Dbar_yy Ez at x, x+1
+    const f2 N = sub(fma(c.c6, dyz_r, ez[1][2]), fma(c.c6, dyz_0, ez[1][1]));
+    const f2 Np = sub(fma(c.c6, dxz_p, ez[2][1]), fma(c.c6, dxz_0, ez[1][1]));
+    const f2 T = fma(c.axy, d2(dxz_p, dxz_0, dxz_m), fma(c.ay, dyz_0, mul(c.ax, dxz_0)));
+    const f2 X = sub(fma(c.c6, P, ex_0), fma(c.c6, Pl, exl_0));
+    const f2 Y = sub(fma(c.c6, Q, ey_0), fma(c.c6, Qm, ey_m));
+    PlaneTerms t;
+    t.zh = fma(c.byz, Y, mul(c.bzx, X));
+    t.zt = sub(T, t.zh);
+    const f2 bN = mul(c.bzx, N), bNp = mul(c.byz, Np);
+    t.x1 = fma(bxy6, G, fma(c.ayz, P, mul(c.az, ex_0)));
+    t.x0 = fma(t.x1, m2(), add(bN, fma(c.bxy, G, mul(c.ay, P))));
+    t.xl = sub(t.x1, bN);
+    t.y1 = fma(bxy6, Gp, fma(c.azx, Q, mul(c.az, ey_0)));
+    t.y0 = fma(t.y1, m2(), add(bNp, fma(c.bxy, Gp, mul(c.ax, Q))));
+    t.yl = sub(t.y1, bNp);
+    return t;
+}
+
+// out = dEp + A in, or with UPD: E = E + dEp + A in (the last sweep and the
+// update of the step in one pass; E in place).  The CTA marches its input
+// planes z0-1..z1 once each: iteration i reads plane z0-1+i from the ring
+// (nothing else of the plane is read again), adds its terms to the partial
+// outputs held in registers, and completes output plane z0+i-2.  One plane
+// is read while the next RS-1 are on their way; one barrier per plane.
+template <bool UPD>
+__global__ void __launch_bounds__(NTH, UPD ? 2 : 3) k3_sweep2(Geo g, Coef3P c, const float *p0, const float *p1,
+                                                             const float *p2, const float *i0, const float *i1,
+                                                             const float *i2, float *o0, float *o1, float *o2) {
+    using namespace pair2;
+    constexpr int RS = SWEEP_RS;
     extern __shared__ __align__(16) unsigned char m3raw[];
     float *ring = reinterpret_cast<float *>(m3raw);  // [RS][3][PL2]
     const float *in[3] = {i0, i1, i2};
@@ -373,190 +457,222 @@ __global__ void __launch_bounds__(NTH, 2) k3_sweep2(Geo g, Coef3P c, const float
     float *out[3] = {o0, o1, o2};
     const int x0 = blockIdx.x * TX2, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * ZSEG, z1 = min(z0 + ZSEG, g.nz);
+    const int np = z1 - z0 + 2;  // input planes z0-1 .. z1
     PairCopies cp;
-    cp.init(g, x0, y0);
+    cp.init(g, x0, y0, z0 - 1);
     const int px = x0 + 2 * threadIdx.x, py = y0 + threadIdx.y;
     const bool inside = px < g.nx && py < g.ny;
-    const int64_t cell = (int64_t)py * g.pitch + px;
     const int c0 = (threadIdx.y + 1) * RW2 + 2 + 2 * threadIdx.x;
-    auto issue = [&](int m) {
-        if (m == 0) {
-            cp.issue<RS>(ring, in, g, z0 - 1);
-            cp.issue<RS>(ring, in, g, z0);
-        }
-        if (z0 + 1 + m <= z1) cp.issue<RS>(ring, in, g, z0 + 1 + m);
+    // copy group i: input plane z0-1+i (empty past the last)
+    auto issue = [&](int i) {
+        if (i < np) cp.issue_next<RS>(ring, in, g);
         cp_async_commit();
     };
-    // dE' of the own pair, planes k and k+1: two register buffers
-    f2 pd[2][3];
-    auto ldown = [&](int k, int b) {
+#pragma unroll
+    for (int i = 0; i < RS - 1; ++i) issue(i);
+    // own-pair offsets: of the output completed next, and of the one two
+    // planes later (the register prefetch); outputs lie in [z0, z1), no wrap
+    int64_t ocell = (int64_t)z0 * g.plane + (int64_t)py * g.pitch + px;
+    int64_t pcell = ocell;
+    // dE' (and E^n) of the own pair of outputs o and o+1: two register buffers
+    f2 pd[2][3], pe[2][3];
+    auto prefetch = [&](int b, bool ok) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             pd[b][q] = mk(0.f, 0.f);
-            if (inside && k < z1) pd[b][q] = __ldg(reinterpret_cast<const float2 *>(dp[q] + (int64_t)k * g.plane + cell));
+            pe[b][q] = mk(0.f, 0.f);
+            if (ok) {
+                pd[b][q] = __ldg(reinterpret_cast<const float2 *>(dp[q] + pcell));
+                if (UPD) pe[b][q] = *reinterpret_cast<const float2 *>(out[q] + pcell);
+            }
         }
+        pcell += g.plane;
     };
-#pragma unroll
-    for (int m = 0; m < LA; ++m) issue(m);
-    ldown(z0, 0);
-    ldown(z0 + 1, 1);
-    f2 en[3];  // UPD: E^n of the own pair, plane k
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-        en[q] = (UPD && inside) ? *reinterpret_cast<const float2 *>(out[q] + (int64_t)z0 * g.plane + cell) : mk(0.f, 0.f);
-    auto step = [&](int k, auto bsel) {
+    prefetch(0, inside);
+    prefetch(1, inside && z0 + 1 < z1);
+    const f2 bxy6 = mul(c.bxy, c.c6);
+    f2 xa = mk(0.f, 0.f), xb = xa, ya = xa, yb = xa, za = xa;  // partial outputs o, o+1
+    auto step = [&](int i, auto bsel) {
         constexpr int b = decltype(bsel)::value;
-        cp_async_wait<LA - 1>();
+        cp_async_wait<RS - 2>();
         __syncthreads();
-        issue(k - z0 + LA);
-        f2 d[3];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) d[q] = pd[b][q];
-        ldown(k + 2, b);
+        issue(i + RS - 1);
         if (inside) {
-            const int sm1 = ((k - 1) & (RS - 1)) * 3 * PL2, s0 = (k & (RS - 1)) * 3 * PL2,
-                      sp1 = ((k + 1) & (RS - 1)) * 3 * PL2;
-            auto V = [&](int q, int dx, int dy, int dz) -> f2 {
-                const float *row = ring + (dz < 0 ? sm1 : (dz > 0 ? sp1 : s0)) + q * PL2 + c0 + dy * RW2;
+            const float *pl = ring + ((z0 - 1 + i) & (RS - 1)) * 3 * PL2 + c0;  // the copy's slot of plane z0-1+i
+            auto V = [&](int q, int dx, int dy) -> f2 {
+                const float *row = pl + q * PL2 + dy * RW2;
                 const f2 pr = *reinterpret_cast<const float2 *>(row);
                 return dx == 0 ? pr : (dx > 0 ? mk(pr.y, row[2]) : mk(row[-1], pr.x));
             };
-            f2 r[3] = {add(d[0], apply_a2<0>(V, c)), add(d[1], apply_a2<1>(V, c)), add(d[2], apply_a2<2>(V, c))};
-            const int64_t idx = (int64_t)k * g.plane + cell;
+            const PlaneTerms t = plane_terms(V, c, bxy6);
+            if (i >= 2) {
+                // output plane z0 + i - 2 is complete
+                f2 r[3] = {add(xa, t.x1), add(ya, t.y1), add(za, t.zh)};
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                if (UPD) r[q] = add(en[q], r[q]);
-                *reinterpret_cast<float2 *>(out[q] + idx) = r[q];
+                for (int q = 0; q < 3; ++q) {
+                    r[q] = add(pd[b][q], r[q]);
+                    if (UPD) r[q] = add(pe[b][q], r[q]);
+                    *reinterpret_cast<float2 *>(out[q] + ocell) = r[q];
+                }
+                ocell += g.plane;
+                prefetch(b, z0 + i < z1);  // output z0 + i, two iterations on
             }
-        }
-        // UPD: E^n of the own pair of the next plane, in flight across the barrier
-        if (UPD && inside && k + 1 < z1) {
-#pragma unroll
-            for (int q = 0; q < 3; ++q)
-                en[q] = *reinterpret_cast<const float2 *>(out[q] + (int64_t)(k + 1) * g.plane + cell);
+            xa = add(xb, t.x0);
+            xb = t.xl;
+            ya = add(yb, t.y0);
+            yb = t.yl;
+            za = t.zt;
         }
     };
-    for (int k = z0; k < z1; k += 2) {
-        step(k, std::integral_constant<int, 0>());
-        if (k + 1 < z1) step(k + 1, std::integral_constant<int, 1>());
+    for (int i = 0; i < np; i += 2) {
+        step(i, std::integral_constant<int, 0>());
+        if (i + 1 < np) step(i + 1, std::integral_constant<int, 1>());
     }
     cp_async_wait<0>();
 }
 
-// dE' = C_b (alpha B) - q F j on a column pair (the source of k3_source,
-// curl_alpha_b in stencil.cuh), 3D; F = one (1/4, 1/2, 1/4) pass along each
-// axis (PASSES = 1) or none.  Ring: B (and j) planes of the 64 x 8 tile,
-// RS slots.
-template <int A, typename F>
-__device__ __forceinline__ f2 curl_alpha_b2(const F &V, const Coef3P &c) {
+// dE' = C_b (alpha B) - q F j on a column pair, 3D (the source of k3_source,
+// curl_alpha_b in stencil.cuh); F = one (1/4, 1/2, 1/4) pass along each axis
+// (PASSES = 1) or none.  The averaged curl (Eqs. ampere_aux_x..z) factored
+// like the sweep's A, the z-differences moved outside:
+//   x: k_y (V_k + c6 Dzz V) - k_z (U_k - U_(k-1)),    V = Dbar_y(bwd) Bz,  U = By + c6 Dbar_yy By,
+//   y: k_z (W_k - W_(k-1)) - k_x (V'_k + c6 Dzz V'),  V' = Dbar_x(bwd) Bz, W = Bx + c6 Dbar_xx Bx,
+//   z: k_x Dbar_x(bwd) U - k_y Dbar_y(bwd) W          (in-plane),
+// so plane j of B reaches outputs j-1, j, j+1 through terms of plane j alone.
+struct CurlTerms {
+    f2 x1, x0, xl;  // x: to outputs j-1 and j+1 (x1), to j (x0), to j+1 (xl = x1 + k_z U)
+    f2 y1, y0, yl;  // y: the same with V' and W
+    f2 z;           // z: to output j
+};
+
+template <typename F>
+__device__ __forceinline__ CurlTerms curl_plane_terms(const F &V, const Coef3P &c, f2 nkxc6, f2 kyc6) {
     using namespace pair2;
-    constexpr int B = (A + 1) % 3, C = (A + 2) % 3;
-    constexpr int bx = B == 0, by = B == 1, bz = B == 2, cx = C == 0, cy = C == 1, cz = C == 2;
-    // k_B Dbar_B(alpha_C B_C), backward along B
-    const f2 v0 = fma(c.c6, d2p<C, C>(V, 0, 0, 0), V(C, 0, 0, 0));
-    const f2 v1 = fma(c.c6, d2p<C, C>(V, -bx, -by, -bz), V(C, -bx, -by, -bz));
-    f2 r = mul(ck<B>(c), fma(v1, m1(), v0));
-    // - k_C Dbar_C(alpha_B B_B), backward along C
-    const f2 u0 = fma(c.c6, d2p<B, B>(V, 0, 0, 0), V(B, 0, 0, 0));
-    const f2 u1 = fma(c.c6, d2p<B, B>(V, -cx, -cy, -cz), V(B, -cx, -cy, -cz));
-    return fma(mul(ck<C>(c), fma(u1, m1(), u0)), m1(), r);
+    auto d2 = [](f2 p, f2 o, f2 m) { return fma(o, m2(), add(p, m)); };  // p - 2 o + m
+    auto sub = [](f2 a, f2 b) { return fma(b, m1(), a); };
+    // Bx at columns x-1..x+1 and rows y-1, y
+    const f2 bx_m = V(0, 0, -1), bx_0 = V(0, 0, 0);
+    const f2 bxl_m = V(0, -1, -1), bxl_0 = V(0, -1, 0), bxr_m = V(0, 1, -1), bxr_0 = V(0, 1, 0);
+    // By at columns x-1, x and rows y-1..y+1
+    const f2 by_m = V(1, 0, -1), by_0 = V(1, 0, 0), by_p = V(1, 0, 1);
+    const f2 byl_m = V(1, -1, -1), byl_0 = V(1, -1, 0), byl_p = V(1, -1, 1);
+    // Bz at (x, y-1), (x, y), (x-1, y)
+    const f2 bz_m = V(2, 0, -1), bz_0 = V(2, 0, 0), bzl_0 = V(2, -1, 0);
+    const f2 U = fma(c.c6, d2(by_p, by_0, by_m), by_0), Ul = fma(c.c6, d2(byl_p, byl_0, byl_m), byl_0);
+    const f2 W = fma(c.c6, d2(bxr_0, bx_0, bxl_0), bx_0), Wm = fma(c.c6, d2(bxr_m, bx_m, bxl_m), bx_m);
+    const f2 Vy = sub(bz_0, bz_m), Vx = sub(bz_0, bzl_0);
+    const f2 kzU = mul(c.kz, U), kzW = mul(c.kz, W);
+    CurlTerms t;
+    t.x1 = mul(kyc6, Vy);
+    t.x0 = fma(t.x1, m2(), sub(mul(c.ky, Vy), kzU));
+    t.xl = add(t.x1, kzU);
+    t.y1 = mul(nkxc6, Vx);
+    t.y0 = fma(t.y1, m2(), sub(kzW, mul(c.kx, Vx)));
+    t.yl = sub(t.y1, kzW);
+    t.z = sub(mul(c.kx, sub(U, Ul)), mul(c.ky, sub(W, Wm)));
+    return t;
 }
 
+// Ring: B (and j) planes of the 64 x 8 tile, RS slots.  The CTA marches its
+// input planes z0-1..z1 once each, like the sweep: iteration i reads plane
+// z0-1+i (B for the curl terms, j for its x-y binomial), and completes output
+// plane z0+i-2; the z part of the binomial combines the x-y results of the
+// last three planes, kept in registers.  One plane is read while the next
+// RS-1 are on their way; one barrier per plane.
 template <int RS, int PASSES, bool HJ>
 __global__ void __launch_bounds__(NTH, 3) k3_source2(Geo g, Coef3P c, const float *b0, const float *b1,
                                                     const float *b2, const float *j0, const float *j1,
                                                     const float *j2, float *o0, float *o1, float *o2) {
     using namespace pair2;
     constexpr int N = HJ ? 6 : 3;
-    constexpr int LA = RS - 3;
     extern __shared__ __align__(16) unsigned char m3raw[];
     float *ring = reinterpret_cast<float *>(m3raw);  // [RS][N][PL2]
     const float *src[6] = {b0, b1, b2, j0, j1, j2};
     float *out[3] = {o0, o1, o2};
     const int x0 = blockIdx.x * TX2, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * ZSEG, z1 = min(z0 + ZSEG, g.nz);
+    const int np = z1 - z0 + 2;  // input planes z0-1 .. z1
     PairCopies cp;
-    cp.init(g, x0, y0);
+    cp.init(g, x0, y0, z0 - 1);
     const int px = x0 + 2 * threadIdx.x, py = y0 + threadIdx.y;
     const bool inside = px < g.nx && py < g.ny;
-    const int64_t cell = (int64_t)py * g.pitch + px;
     const int c0 = (threadIdx.y + 1) * RW2 + 2 + 2 * threadIdx.x;
-    auto issue = [&](int m) {
-        if (m == 0) {
-            cp.issue<RS, N>(ring, src, g, z0 - 1);
-            cp.issue<RS, N>(ring, src, g, z0);
-        }
-        if (z0 + 1 + m <= z1) cp.issue<RS, N>(ring, src, g, z0 + 1 + m);
+    // copy group i: input plane z0-1+i (empty past the last)
+    auto issue = [&](int i) {
+        if (i < np) cp.issue_next<RS, N>(ring, src, g);
         cp_async_commit();
     };
 #pragma unroll
-    for (int m = 0; m < LA; ++m) issue(m);
-    f2 jz[3][2];  // x-y filtered current of planes k-1, k (own pair)
-    if constexpr (HJ && PASSES == 1) {
-        // planes z0-1 and z0 (copy group 0)
-        cp_async_wait<LA - 1>();
+    for (int i = 0; i < RS - 1; ++i) issue(i);
+    int64_t ocell = (int64_t)z0 * g.plane + (int64_t)py * g.pitch + px;
+    const f2 nkxc6 = mul(mul(c.kx, c.c6), m1()), kyc6 = mul(c.ky, c.c6);
+    f2 xa = mk(0.f, 0.f), xb = xa, ya = xa, yb = xa, za = xa;  // partial outputs o, o+1
+    // PASSES = 1: x-y binomial of the current of planes j-2, j-1 (own pair);
+    // PASSES = 0: the raw current of plane j-1 in jz[a][1]
+    f2 jz[3][2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) jz[a][0] = jz[a][1] = xa;
+    for (int i = 0; i < np; ++i) {
+        cp_async_wait<RS - 2>();
         __syncthreads();
+        issue(i + RS - 1);
         if (inside) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float *pl = ring + ((z0 - 1 + h) & (RS - 1)) * N * PL2 + (3 + a) * PL2 + c0;
-                    f2 acc = mk(0.f, 0.f);
-#pragma unroll
-                    for (int dy = -1; dy <= 1; ++dy) {
-                        const float *row = pl + dy * RW2;
-                        const f2 pr = *reinterpret_cast<const float2 *>(row);
-                        const f2 rowf = fma(pr, cst(2), add(mk(row[-1], pr.x), mk(pr.y, row[2])));
-                        acc = fma(cst(2 - dy * dy), rowf, acc);
-                    }
-                    jz[a][h] = acc;
-                }
-        }
-    }
-    for (int k = z0; k < z1; ++k) {
-        cp_async_wait<LA - 1>();
-        __syncthreads();
-        issue(k - z0 + LA);
-        if (inside) {
-            const int sm1 = ((k - 1) & (RS - 1)) * N * PL2, s0 = (k & (RS - 1)) * N * PL2,
-                      sp1 = ((k + 1) & (RS - 1)) * N * PL2;
-            auto V = [&](int q, int dx, int dy, int dz) -> f2 {
-                const float *row = ring + (dz < 0 ? sm1 : (dz > 0 ? sp1 : s0)) + q * PL2 + c0 + dy * RW2;
+            const float *pl = ring + ((z0 - 1 + i) & (RS - 1)) * N * PL2 + c0;  // the copy's slot of plane z0-1+i
+            auto V = [&](int q, int dx, int dy) -> f2 {
+                const float *row = pl + q * PL2 + dy * RW2;
                 const f2 pr = *reinterpret_cast<const float2 *>(row);
                 return dx == 0 ? pr : (dx > 0 ? mk(pr.y, row[2]) : mk(row[-1], pr.x));
             };
-            f2 d[3] = {curl_alpha_b2<0>(V, c), curl_alpha_b2<1>(V, c), curl_alpha_b2<2>(V, c)};
+            const CurlTerms t = curl_plane_terms(V, c, nkxc6, kyc6);
+            f2 jn[3];
             if constexpr (HJ) {
-                if constexpr (PASSES == 1) {
-                    // separable binomial, integer weights (1, 2, 1) per axis, 1/64 folded
-                    // into q: the x-y part of plane k+1 from the ring, the z part from the
-                    // x-y results of planes k-1, k, k+1 kept in registers
-                    auto jxy = [&](int a, int dz) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if constexpr (PASSES == 1) {
+                        // separable binomial with integer weights (1, 2, 1) per axis,
+                        // the 1/64 folded into q: the x-y part here
                         f2 acc = mk(0.f, 0.f);
 #pragma unroll
                         for (int dy = -1; dy <= 1; ++dy) {
-                            const f2 rowf = fma(V(3 + a, 0, dy, dz), cst(2), add(V(3 + a, -1, dy, dz), V(3 + a, 1, dy, dz)));
+                            const f2 rowf = fma(V(3 + a, 0, dy), cst(2), add(V(3 + a, -1, dy), V(3 + a, 1, dy)));
                             acc = fma(cst(2 - dy * dy), rowf, acc);
                         }
-                        return acc;
-                    };
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        const f2 jn = jxy(a, 1);
-                        const f2 jsum = fma(jz[a][1], cst(2), add(jz[a][0], jn));
-                        jz[a][0] = jz[a][1];
-                        jz[a][1] = jn;
-                        d[a] = fma(mul(c.q64, jsum), m1(), d[a]);
+                        jn[a] = acc;
+                    } else {
+                        jn[a] = V(3 + a, 0, 0);
                     }
-                } else {
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) d[a] = fma(mul(c.q, V(3 + a, 0, 0, 0)), m1(), d[a]);
                 }
             }
-            const int64_t idx = (int64_t)k * g.plane + cell;
+            if (i >= 2) {
+                // output plane z0 + i - 2 is complete
+                f2 d[3] = {add(xa, t.x1), add(ya, t.y1), za};
+                if constexpr (HJ) {
 #pragma unroll
-            for (int q = 0; q < 3; ++q) *reinterpret_cast<float2 *>(out[q] + idx) = d[q];
+                    for (int a = 0; a < 3; ++a) {
+                        if constexpr (PASSES == 1) {
+                            const f2 jsum = fma(jz[a][1], cst(2), add(jz[a][0], jn[a]));
+                            d[a] = fma(mul(c.q64, jsum), m1(), d[a]);
+                        } else {
+                            d[a] = fma(mul(c.q, jz[a][1]), m1(), d[a]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 3; ++q) *reinterpret_cast<float2 *>(out[q] + ocell) = d[q];
+                ocell += g.plane;
+            }
+            xa = add(xb, t.x0);
+            xb = t.xl;
+            ya = add(yb, t.y0);
+            yb = t.yl;
+            za = t.z;
+            if constexpr (HJ) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    jz[a][0] = jz[a][1];
+                    jz[a][1] = jn[a];
+                }
+            }
         }
     }
     cp_async_wait<0>();
@@ -584,14 +700,15 @@ __global__ void __launch_bounds__(NTH, 3) k3_faraday2(Geo g, Coef3P c, const flo
     const int x0 = blockIdx.x * TX2, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * ZSEG, z1 = min(z0 + ZSEG, g.nz);
     PairCopies cp;
-    cp.init(g, x0, y0);
+    cp.init(g, x0, y0, z0);
     const int px = x0 + 2 * threadIdx.x, py = y0 + threadIdx.y;
     const bool inside = px < g.nx && py < g.ny;
     const int64_t cell = (int64_t)py * g.pitch + px;
     const int c0 = (threadIdx.y + 1) * RW2 + 2 + 2 * threadIdx.x;
+    // copy group m: planes z0, z0+1 (m = 0), plane z0+1+m (m >= 1, up to z1)
     auto issue = [&](int m) {
-        if (m == 0) cp.issue<RS>(ring, in, g, z0);
-        if (z0 + 1 + m <= z1) cp.issue<RS>(ring, in, g, z0 + 1 + m);
+        if (m == 0) cp.issue_next<RS>(ring, in, g);
+        if (z0 + 1 + m <= z1) cp.issue_next<RS>(ring, in, g);
         cp_async_commit();
     };
     // B of the own pair, planes k and k+1: two register buffers
@@ -822,7 +939,7 @@ bool pair_path(const Geo &, double *) { return false; }
 template <bool UPD>
 void run_sweep2(const Geo &g, const Coef<float> &c, const float *const dEp[3], const float *const in[3],
                 float *const out[3], cudaStream_t s) {
-    constexpr size_t bytes = (size_t)RingDepth<float>::RS * 3 * PL2 * sizeof(float);
+    constexpr size_t bytes = (size_t)SWEEP_RS * 3 * PL2 * sizeof(float);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k3_sweep2<UPD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
