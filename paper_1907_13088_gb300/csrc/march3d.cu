@@ -755,25 +755,24 @@ __global__ void __launch_bounds__(NTH, 3) k3_faraday2(Geo g, Coef3P c, const flo
 
 // ---------------------------------------------------------------------------
 // Two sweeps of Algorithm 1 in one z-march (temporal blocking, FP32 column
-// pairs, even n_x): dE_(s+2) = dE' + A (dE' + A dE_(s)).  The first sweep (A
-// stage) is evaluated on the output tile grown by one cell on every side in
-// x and y (34 pairs x 10 rows around the 32 x 8 pairs of the tile), from an
-// input ring whose planes carry a halo of two; its results stay in a second
-// shared-memory ring that the second sweep (B stage) reads two planes behind,
-// so dE_(s+1) never leaves the SM.  352 threads: every thread but the last 12
-// owns a first-sweep pair, the first 256 also the second-sweep pair of the
-// tile.  One barrier per plane.  With UPD the second sweep also applies
-// E^{n+1} = E^n + dE (E in place).  Two CTAs per SM (80 registers, 76 KB of
-// shared memory, one input plane in flight) measured faster than one CTA
-// with five planes in flight (256^3: 1.60 vs 1.83 ms per step); both are
-// slower than one sweep per pass (1.06 ms): the grown tile and the lower
-// occupancy cost more on-chip work than the saved HBM traffic returns.
+// pairs, even n_x): dE_(s+2) = dE' + A (dE' + A dE_(s)), both sweeps in the
+// factored form of plane_terms.  The first sweep (A stage) is evaluated on the
+// output tile grown by one cell on every side in x and y (34 pairs x 10 rows
+// around the 32 x 8 pairs of the tile), from an input ring whose planes carry
+// a halo of two; each plane of dE_(s+1) it completes goes into one of two
+// shared-memory plane buffers, which the second sweep (B stage) reads one
+// iteration later, so dE_(s+1) never leaves the SM.  352 threads: every
+// thread but the last 12 owns a first-sweep pair, the first 256 also the
+// second-sweep pair of the tile.  Iteration i: the A stage reads input plane
+// z0-2+i and completes first-sweep plane z0+i-3; the B stage reads
+// first-sweep plane z0+i-4 and completes output plane z0+i-5.  One barrier
+// per iteration.  With UPD the second sweep also applies E^{n+1} = E^n + dE
+// (E in place).
 constexpr int FRW = 72;                // floats per row: column x0 + j at index j + 4, j in [-4, 67]
 constexpr int FIR = 12, FAR = 10;      // rows of an input plane (y0-2..y0+9) and of a first-sweep plane (y0-1..y0+8)
 constexpr int FIPL = FRW * FIR, FAPL = FRW * FAR;
 constexpr int FNT = 352, FNA = 340, FNB = 256;
-constexpr int FRS = 4, FLA = FRS - 3;  // input ring slots, planes in flight (2 CTAs per SM)
-constexpr int FAS = 4;                 // first-sweep ring slots
+constexpr int FRS = 4;                 // input ring slots: one plane read, three in flight
 constexpr int FNI = (FRW / 2) * FIR;   // pair copies per input plane and component (432)
 
 template <bool UPD>
@@ -783,14 +782,17 @@ __global__ void __launch_bounds__(FNT, 2) k3_sweeps2f(Geo g, Coef3P c, const flo
     using namespace pair2;
     extern __shared__ __align__(16) unsigned char m3raw[];
     float *ring = reinterpret_cast<float *>(m3raw);  // [FRS][3][FIPL] input planes, halo 2
-    float *aring = ring + FRS * 3 * FIPL;             // [FAS][3][FAPL] first-sweep planes, halo 1
+    float *abuf = ring + FRS * 3 * FIPL;              // [2][3][FAPL] first-sweep planes, halo 1
     const float *in[3] = {i0, i1, i2};
     const float *dp[3] = {p0, p1, p2};
     float *out[3] = {o0, o1, o2};
     const int x0 = blockIdx.x * TX2, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * ZSEG, z1 = min(z0 + ZSEG, g.nz);
+    const int nin = z1 - z0 + 4;  // input planes z0-2 .. z1+1
     const int tid = threadIdx.x;
-    // input copy items of this thread (pairs of columns, periodic wrap)
+    const int64_t vol = (int64_t)g.nz * g.plane;
+    // input copy items of this thread (pairs of columns, periodic wrap), and
+    // the wrapped offset of the plane copied next
     int cs[2], co[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -803,24 +805,20 @@ __global__ void __launch_bounds__(FNT, 2) k3_sweeps2f(Geo g, Coef3P c, const flo
             co[r] = wrapm(y0 - 2 + row, g.ny) * (int)g.pitch + wrapm(x0 + j, g.nx);
         }
     }
-    auto issue_plane = [&](int k) {
-        const int64_t base = (int64_t)wrapm(k, g.nz) * g.plane;
-        float *slot = ring + (k & (FRS - 1)) * 3 * FIPL;
+    int64_t koff = (int64_t)wrapm(z0 - 2, g.nz) * g.plane;
+    // copy group i: input plane z0-2+i (empty past the last)
+    auto issue = [&](int i) {
+        if (i < nin) {
+            float *slot = ring + ((z0 - 2 + i) & (FRS - 1)) * 3 * FIPL;
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            if (cs[r] < 0) continue;
+            for (int r = 0; r < 2; ++r) {
+                if (cs[r] < 0) continue;
+                const int64_t go = koff + co[r];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) cp_async_pair(slot + q * FIPL + cs[r], in[q] + base + co[r]);
-        }
-    };
-    // copy group m: input planes z0-2..z0 (m = 0), plane z0+m (m >= 1, up to z1+1)
-    auto issue = [&](int m) {
-        if (m == 0) {
-            issue_plane(z0 - 2);
-            issue_plane(z0 - 1);
-            issue_plane(z0);
-        } else if (z0 + m <= z1 + 1) {
-            issue_plane(z0 + m);
+                for (int q = 0; q < 3; ++q) cp_async_pair(slot + q * FIPL + cs[r], in[q] + go);
+            }
+            koff += g.plane;
+            if (koff == vol) koff = 0;
         }
         cp_async_commit();
     };
@@ -828,54 +826,90 @@ __global__ void __launch_bounds__(FNT, 2) k3_sweeps2f(Geo g, Coef3P c, const flo
     const bool hasA = tid < FNA, hasB = tid < FNB;
     const int pa = tid % 34 - 1, ra = tid / 34 - 1;  // pair -1..32, row -1..8
     const int pb = tid % 32, rb = tid / 32;          // pair 0..31, row 0..7
-    const int ca = 2 * pa + 4, cb = 2 * pb + 4;      // smem column of the own pair
-    const int64_t cellA = (int64_t)wrapm(y0 + ra, g.ny) * g.pitch + wrapm(x0 + 2 * pa, g.nx);
-    const int64_t cellB = (int64_t)(y0 + rb) * g.pitch + (x0 + 2 * pb);
+    const int cA = (ra + 2) * FRW + 2 * pa + 4;      // input-plane index of the A pair
+    const int wA = (ra + 1) * FRW + 2 * pa + 4;      // first-sweep-plane index of the A pair
+    const int cB = (rb + 1) * FRW + 2 * pb + 4;      // first-sweep-plane index of the B pair
     const bool outB = hasB && x0 + 2 * pb < g.nx && y0 + rb < g.ny;
-    auto ld2 = [&](const float *base, int k, int64_t cell) {
-        return *reinterpret_cast<const float2 *>(base + (int64_t)wrapm(k, g.nz) * g.plane + cell);
+    // own-pair offsets: A's dE' of its next plane (wrapped periodically: the
+    // grown tile reaches planes z0-1 and z1), B's next output plane
+    const int cellA = wrapm(y0 + ra, g.ny) * (int)g.pitch + wrapm(x0 + 2 * pa, g.nx);
+    int64_t aoff = (int64_t)wrapm(z0 - 1, g.nz) * g.plane;
+    int64_t bcell = (int64_t)z0 * g.plane + (int64_t)(y0 + rb) * g.pitch + (x0 + 2 * pb);
+    f2 pa_d[3], pb_d[3], pb_e[3];  // dE' of A's next plane; dE' (and E^n) of B's next output
+    auto load_a = [&]() {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) pa_d[q] = __ldg(reinterpret_cast<const float2 *>(dp[q] + aoff + cellA));
+        aoff += g.plane;
+        if (aoff == vol) aoff = 0;
+    };
+    // B's output plane at offset `at` (bcell, or the plane after it)
+    auto load_b = [&](bool ok, int64_t at) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            pb_d[q] = ok ? __ldg(reinterpret_cast<const float2 *>(dp[q] + at)) : mk(0.f, 0.f);
+            if (UPD) pb_e[q] = ok ? *reinterpret_cast<const float2 *>(out[q] + at) : mk(0.f, 0.f);
+        }
     };
 #pragma unroll
-    for (int m = 0; m < FLA; ++m) issue(m);
-    for (int k = z0 - 1; k <= z1 + 1; ++k) {
-        const int it = k - (z0 - 1);
-        cp_async_wait<FLA - 1>();
+    for (int i = 0; i < FRS - 1; ++i) issue(i);
+    const f2 bxy6 = mul(c.bxy, c.c6);
+    f2 ax_a = mk(0.f, 0.f), ax_b = ax_a, ay_a = ax_a, ay_b = ax_a, az_a = ax_a;  // A: partial planes o, o+1
+    f2 bx_a = ax_a, bx_b = ax_a, by_a = ax_a, by_b = ax_a, bz_a = ax_a;          // B: the same
+    for (int i = 0; i < nin + 1; ++i) {
+        cp_async_wait<FRS - 2>();
         __syncthreads();
-        issue(it + FLA);
-        // A stage: dE_(s+1) of plane k on the grown tile
-        if (hasA && k <= z1) {
-            const int sm1 = ((k - 1) & (FRS - 1)) * 3 * FIPL, s0 = (k & (FRS - 1)) * 3 * FIPL,
-                      sp1 = ((k + 1) & (FRS - 1)) * 3 * FIPL;
-            const int cA = (ra + 2) * FRW + ca;
-            auto V = [&](int q, int dx, int dy, int dz) -> f2 {
-                const float *row = ring + (dz < 0 ? sm1 : (dz > 0 ? sp1 : s0)) + q * FIPL + cA + dy * FRW;
+        issue(i + FRS - 1);
+        // A stage: input plane z0-2+i; completes first-sweep plane z0+i-3 (i >= 2)
+        if (hasA && i < nin) {
+            if (i == 1) load_a();  // dE' of plane z0-1
+            const float *pl = ring + ((z0 - 2 + i) & (FRS - 1)) * 3 * FIPL + cA;
+            auto V = [&](int q, int dx, int dy) -> f2 {
+                const float *row = pl + q * FIPL + dy * FRW;
                 const f2 pr = *reinterpret_cast<const float2 *>(row);
                 return dx == 0 ? pr : (dx > 0 ? mk(pr.y, row[2]) : mk(row[-1], pr.x));
             };
-            float *dst = aring + (k & (FAS - 1)) * 3 * FAPL + (ra + 1) * FRW + ca;
-            *reinterpret_cast<float2 *>(dst) = add(ld2(dp[0], k, cellA), apply_a2<0>(V, c));
-            *reinterpret_cast<float2 *>(dst + FAPL) = add(ld2(dp[1], k, cellA), apply_a2<1>(V, c));
-            *reinterpret_cast<float2 *>(dst + 2 * FAPL) = add(ld2(dp[2], k, cellA), apply_a2<2>(V, c));
-        }
-        // B stage: dE_(s+2) of plane k-2 on the tile, from first-sweep planes k-3..k-1
-        const int kb = k - 2;
-        if (outB && kb >= z0 && kb < z1) {
-            const int sm1 = ((kb - 1) & (FAS - 1)) * 3 * FAPL, s0 = (kb & (FAS - 1)) * 3 * FAPL,
-                      sp1 = ((kb + 1) & (FAS - 1)) * 3 * FAPL;
-            const int cB = (rb + 1) * FRW + cb;
-            auto V = [&](int q, int dx, int dy, int dz) -> f2 {
-                const float *row = aring + (dz < 0 ? sm1 : (dz > 0 ? sp1 : s0)) + q * FAPL + cB + dy * FRW;
-                const f2 pr = *reinterpret_cast<const float2 *>(row);
-                return dx == 0 ? pr : (dx > 0 ? mk(pr.y, row[2]) : mk(row[-1], pr.x));
-            };
-            f2 r[3] = {add(ld2(dp[0], kb, cellB), apply_a2<0>(V, c)), add(ld2(dp[1], kb, cellB), apply_a2<1>(V, c)),
-                       add(ld2(dp[2], kb, cellB), apply_a2<2>(V, c))};
-            const int64_t idx = (int64_t)kb * g.plane + cellB;
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                if (UPD) r[q] = add(*reinterpret_cast<const float2 *>(out[q] + idx), r[q]);
-                *reinterpret_cast<float2 *>(out[q] + idx) = r[q];
+            const PlaneTerms t = plane_terms(V, c, bxy6);
+            if (i >= 2) {
+                float *dst = abuf + ((z0 + i - 3) & 1) * 3 * FAPL + wA;
+                *reinterpret_cast<float2 *>(dst) = add(pa_d[0], add(ax_a, t.x1));
+                *reinterpret_cast<float2 *>(dst + FAPL) = add(pa_d[1], add(ay_a, t.y1));
+                *reinterpret_cast<float2 *>(dst + 2 * FAPL) = add(pa_d[2], add(az_a, t.zh));
+                if (i + 1 < nin) load_a();  // dE' of plane z0+i-2, next iteration
             }
+            ax_a = add(ax_b, t.x0);
+            ax_b = t.xl;
+            ay_a = add(ay_b, t.y0);
+            ay_b = t.yl;
+            az_a = t.zt;
+        }
+        // B stage: first-sweep plane z0+i-4 (i >= 3); completes output plane z0+i-5 (i >= 5)
+        if (hasB && i >= 3) {
+            if (i == 4) load_b(outB, bcell);  // output z0
+            const float *pl = abuf + ((z0 + i - 4) & 1) * 3 * FAPL + cB;
+            auto V = [&](int q, int dx, int dy) -> f2 {
+                const float *row = pl + q * FAPL + dy * FRW;
+                const f2 pr = *reinterpret_cast<const float2 *>(row);
+                return dx == 0 ? pr : (dx > 0 ? mk(pr.y, row[2]) : mk(row[-1], pr.x));
+            };
+            const PlaneTerms t = plane_terms(V, c, bxy6);
+            if (i >= 5) {
+                f2 r[3] = {add(bx_a, t.x1), add(by_a, t.y1), add(bz_a, t.zh)};
+                if (outB) {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        r[q] = add(pb_d[q], r[q]);
+                        if (UPD) r[q] = add(pb_e[q], r[q]);
+                        *reinterpret_cast<float2 *>(out[q] + bcell) = r[q];
+                    }
+                }
+                bcell += g.plane;
+                load_b(outB && z0 + i - 4 < z1, bcell);  // output z0+i-4, next iteration
+            }
+            bx_a = add(bx_b, t.x0);
+            bx_b = t.xl;
+            by_a = add(by_b, t.y0);
+            by_b = t.yl;
+            bz_a = t.zt;
         }
     }
     cp_async_wait<0>();
@@ -954,7 +988,7 @@ void run_sweep2(const Geo &g, const Coef<float> &c, const float *const dEp[3], c
 template <bool UPD>
 void run_sweeps2f(const Geo &g, const Coef<float> &c, const float *const dEp[3], const float *const in[3],
                   float *const out[3], cudaStream_t s) {
-    constexpr size_t bytes = ((size_t)FRS * 3 * FIPL + (size_t)FAS * 3 * FAPL) * sizeof(float);
+    constexpr size_t bytes = ((size_t)FRS * 3 * FIPL + (size_t)2 * 3 * FAPL) * sizeof(float);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k3_sweeps2f<UPD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
