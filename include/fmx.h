@@ -529,6 +529,14 @@ fmx_status fmx_step_static(const fmx_params *p, void *const *E, void *const *B, 
  *     normal barrier.
  *   FMX_OPT_RESIDENT_CLUSTERS (read only): clusters of the last resident
  *     launch (0 before the first).
+ *   FMX_OPT_SEGMENT_ROWS: rows of the row segments that the CTAs of the FP32
+ *     2D fused engine (the TE and TM kernels of the step and of the adjoint
+ *     step) each march over, a grid of at most that many rows taking one
+ *     segment; every segment recomputes a few warm-up rows of the row
+ *     pipeline.  0 (default): as many segments as fill one wave of CTAs at
+ *     the kernels' occupancy, but none shorter than 3m + 2p + 8 rows (p: the
+ *     current's filter passes, 0 without a current).  Same results to the
+ *     bit.
  * fmx_set_option returns FMX_EINVAL for an unknown or read-only option or a
  * bad value; fmx_get_option returns the value, or -1 (unknown option or NULL
  * grid). */
@@ -536,7 +544,8 @@ enum {
     FMX_OPT_SWEEPS_PER_PASS = 1,
     FMX_OPT_WAIT_LIMIT_US = 2,
     FMX_OPT_SELFTEST_LOST_ARRIVAL = 3,
-    FMX_OPT_RESIDENT_CLUSTERS = 4
+    FMX_OPT_RESIDENT_CLUSTERS = 4,
+    FMX_OPT_SEGMENT_ROWS = 5
 };
 fmx_status fmx_set_option(fmx_grid *g, int option, int value);
 int fmx_get_option(const fmx_grid *g, int option);

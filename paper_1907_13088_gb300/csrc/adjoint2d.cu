@@ -408,6 +408,10 @@ __global__ void __launch_bounds__(NT, 3)
     }
 }
 
+// rows per segment asked for by the caller of the current launch (0:
+// automatic, see AdjLauncher::run)
+thread_local int t_adj_rows = 0;
+
 template <int POL, int M, int P, bool HJB>
 struct AdjLauncher {
     static constexpr int NT = 128;
@@ -433,10 +437,15 @@ struct AdjLauncher {
             cudaGetDevice(&dev);
             if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
         }
+        // automatic: one wave of CTAs at the measured occupancy, but no
+        // segment shorter than its warm-up rows (3m + 2p + 8), as the forward
         int nseg = blocks_per_sm() * sms / strips;
         if (nseg < 1) nseg = 1;
         if (nseg > g.ny) nseg = g.ny;
-        const int rows = (g.ny + nseg - 1) / nseg;
+        int rows = (g.ny + nseg - 1) / nseg;
+        if (rows < 3 * M + 2 * P + 8) rows = 3 * M + 2 * P + 8;
+        if (t_adj_rows > 0) rows = t_adj_rows;
+        if (rows > g.ny) rows = g.ny;
         const int segs = (g.ny + rows - 1) / rows;
         k_adj2d<POL, M, P, HJB, NT><<<strips * segs, NT, smem_bytes(), s>>>(a, g, c, width, rows, strips);
     }
@@ -470,8 +479,12 @@ bool adjoint2d_supported(const Geo &g, int m, int passes) {
            passes >= 0 && passes <= 3;
 }
 
-int launch_adjoint2d(const Geo &g, const Coef<float> &c, const Adj2dArgs<float> &a, cudaStream_t s) {
+int launch_adjoint2d(const Geo &g, const Coef<float> &c, const Adj2dArgs<float> &a, cudaStream_t s, int seg_rows) {
     if (!adjoint2d_supported(g, a.m, a.passes) || c.c6 != 1.f / 6.f) return -1;
+    struct RowsScope {  // the segment rows of this call's launches
+        explicit RowsScope(int r) { t_adj_rows = r; }
+        ~RowsScope() { t_adj_rows = 0; }
+    } rows_scope(seg_rows);
     Coef2 k;
     auto b = [](float v) { return make_float2(v, v); };
     k.kx = b(c.kx);

@@ -297,6 +297,8 @@ struct fmx_grid {
     cudaEvent_t ev_in = nullptr, ev_comp = nullptr, ev_out = nullptr;
     // sweeps of Algorithm 1 per z-march pass of the 3D kernels (fmx_set_option)
     int sweeps_per_pass = 1;
+    // rows per segment of the FP32 TE/TM kernels, forward and adjoint (0: automatic)
+    int seg_rows = 0;
     // resident engine: limit of a wait at its grid barrier, the self-test of
     // that wait, and the clusters of the last launch
     long long wait_limit_us = 1000000;
@@ -678,7 +680,7 @@ fmx_status fused_step(fmx_grid *g, int nsteps, StepPre pre = nullptr) {
         if constexpr (sizeof(T) == 4) {
             // the TE/TM kernels take alpha's 1/6 as a compile-time constant (lumped mode zeroes it)
             if (fmx::fused2d_pol_supported(g->geo) && c.c6 == 1.f / 6.f) {
-                nl = fmx::launch_fused2d_pol(g->geo, c, a, g->stream, ev, two ? g->s_tm : nullptr);
+                nl = fmx::launch_fused2d_pol(g->geo, c, a, g->stream, ev, two ? g->s_tm : nullptr, g->seg_rows);
                 g->prof_kinds = 2;
             } else {
                 if (ev) cudaEventRecord(ev[0], g->stream);
@@ -756,7 +758,7 @@ fmx_status adjoint_fused(fmx_grid *g, float *const Eb[3], float *const Bb[3], fl
     }
     a.m = g->p.m;
     a.passes = passes;
-    const int n = fmx::launch_adjoint2d(g->geo, make_coef<float>(g->co), a, g->stream);
+    const int n = fmx::launch_adjoint2d(g->geo, make_coef<float>(g->co), a, g->stream, g->seg_rows);
     if (n < 0) return fail(FMX_EUNSUPPORTED, "fused 2D adjoint: configuration not instantiated");
     g->launches += n;
     return check_launch(g, "fused adjoint launch");
@@ -1421,6 +1423,10 @@ fmx_status fmx_set_option(fmx_grid *g, int option, int value) {
             if (value != 0 && value != 1) return fail(FMX_EINVAL, "lost-arrival self-test is 0 or 1 (got %d)", value);
             g->lost_arrival = value;
             return FMX_OK;
+        case FMX_OPT_SEGMENT_ROWS:
+            if (value < 0) return fail(FMX_EINVAL, "segment rows must be >= 0 (got %d)", value);
+            g->seg_rows = value;
+            return FMX_OK;
     }
     return fail(FMX_EINVAL, "unknown option %d", option);
 }
@@ -1432,6 +1438,7 @@ int fmx_get_option(const fmx_grid *g, int option) {
         case FMX_OPT_WAIT_LIMIT_US: return (int)g->wait_limit_us;
         case FMX_OPT_SELFTEST_LOST_ARRIVAL: return g->lost_arrival;
         case FMX_OPT_RESIDENT_CLUSTERS: return g->last_clusters;
+        case FMX_OPT_SEGMENT_ROWS: return g->seg_rows;
     }
     return -1;
 }

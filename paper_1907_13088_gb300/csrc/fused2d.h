@@ -43,9 +43,10 @@ Fused2dShape fused2d_shape(const Geo &g, int m, int passes);
 // of kernels launched or -1.
 bool fused2d_pol_supported(const Geo &g);
 // s_tm: stream for the TM launch (nullptr: s); the caller orders the two
+// seg_rows: rows per segment (0: one wave of CTAs at the measured occupancy)
 int launch_fused2d_pol(const Geo &g, const Coef<float> &c, const Fused2dArgs<float> &a, cudaStream_t s,
-                       cudaEvent_t *ev = nullptr, cudaStream_t s_tm = nullptr);
-Fused2dShape fused2d_pol_shape(const Geo &g, int m, int passes);
+                       cudaEvent_t *ev = nullptr, cudaStream_t s_tm = nullptr, int seg_rows = 0);
+Fused2dShape fused2d_pol_shape(const Geo &g, int m, int passes, int seg_rows = 0);
 
 // Fused 2D adjoint step (adjoint2d.cu), FP32, TE and TM kernels.  Maps
 // (Ebar, Bbar) = dL/d(E^{n+1}, B^{n+3/2}) to dL/d(E^n, B^{n+1/2}) and writes
@@ -66,7 +67,7 @@ struct Adj2dArgs {
 };
 // even nx, 32-bit element offsets; m <= 4, passes <= 3
 bool adjoint2d_supported(const Geo &g, int m, int passes);
-int launch_adjoint2d(const Geo &g, const Coef<float> &c, const Adj2dArgs<float> &a, cudaStream_t s);
+int launch_adjoint2d(const Geo &g, const Coef<float> &c, const Adj2dArgs<float> &a, cudaStream_t s, int seg_rows = 0);
 
 // Batched step (fused2d.cu): independent FP32 grids advanced by one
 // persistent launch per step over (grid, strip, segment) tiles.

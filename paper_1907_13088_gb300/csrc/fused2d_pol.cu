@@ -19,6 +19,10 @@ using namespace pair2;
 using pol2d::PolGeom;
 using pol2d::pol_tile;
 
+// rows per segment asked for by the caller of the current launch (0:
+// automatic, see PolLauncher::shape)
+thread_local int t_rows = 0;
+
 template <int POL, int M, int P, bool HJ, int NT>
 __global__ void __launch_bounds__(NT, 3)
     k_pol2d(Fused2dArgs<float> a, Geo g, Coef2 c, int W, int L, int nstrip) {
@@ -54,11 +58,19 @@ struct PolLauncher {
             cudaGetDevice(&dev);
             if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
         }
+        // automatic: one wave of CTAs at the measured occupancy, but no
+        // segment shorter than the rows its pipeline recomputes to warm up
+        // (3m + 2p + 8): on small grids fewer, longer segments are faster
+        // (1024^2, m = 4, p = 3: 12-row segments 38.6 us per step, 24-row 30.7)
         const int target = blocks_per_sm() * sms;
         int nseg = target / sh.strips;
         if (nseg < 1) nseg = 1;
         if (nseg > g.ny) nseg = g.ny;
-        sh.rows = (g.ny + nseg - 1) / nseg;
+        int rows = (g.ny + nseg - 1) / nseg;
+        const int warm = 3 * M + 2 * (HJ ? P : 0) + 8;
+        if (rows < warm) rows = warm;
+        if (t_rows > 0) rows = t_rows;
+        sh.rows = rows < g.ny ? rows : g.ny;
         sh.segments = (g.ny + sh.rows - 1) / sh.rows;
         return sh;
     }
@@ -126,24 +138,28 @@ Coef2 make_coef2(const Coef<float> &c, int passes) { return pol2d::coef2_of(c, p
 bool fused2d_pol_supported(const Geo &g) { return (int64_t)g.ny * g.pitch < ((int64_t)1 << 31); }
 
 int launch_fused2d_pol(const Geo &g, const Coef<float> &c, const Fused2dArgs<float> &a, cudaStream_t s,
-                       cudaEvent_t *ev, cudaStream_t s_tm) {
+                       cudaEvent_t *ev, cudaStream_t s_tm, int seg_rows) {
     const bool hj = a.J[0] != nullptr;
     const int p = hj ? a.passes : 0;
     if (c.c6 != 1.f / 6.f) return -1;  // the kernels use 1/6 as a compile-time constant
     t_ev = ev;
     t_tm = s_tm;
+    t_rows = seg_rows;
     const int n = pol_dispatch(g, make_coef2(c, p), a, s, a.m, hj, p, nullptr);
     t_ev = nullptr;
     t_tm = nullptr;
+    t_rows = 0;
     return n;
 }
 
-Fused2dShape fused2d_pol_shape(const Geo &g, int m, int passes) {
+Fused2dShape fused2d_pol_shape(const Geo &g, int m, int passes, int seg_rows) {
     Fused2dShape sh{0, 0, 0, 0, 0, 0};
     Fused2dArgs<float> a{};
     Coef<float> c{};
+    t_rows = seg_rows;
     pol_dispatch(g, make_coef2(c, passes >= 0 ? passes : 0), a, nullptr, m, passes >= 0, passes >= 0 ? passes : 0,
                  &sh);
+    t_rows = 0;
     return sh;
 }
 

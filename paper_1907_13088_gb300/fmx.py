@@ -197,6 +197,7 @@ fmx_step_host = _lib.fmx_step_host
 fmx_set_option = _lib.fmx_set_option
 fmx_get_option = _lib.fmx_get_option
 FMX_OPT_SWEEPS_PER_PASS, FMX_OPT_WAIT_LIMIT_US, FMX_OPT_SELFTEST_LOST_ARRIVAL, FMX_OPT_RESIDENT_CLUSTERS = 1, 2, 3, 4
+FMX_OPT_SEGMENT_ROWS = 5
 FMX_STATIC_SCRATCH_BYTES = 4 << 20
 
 

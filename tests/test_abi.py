@@ -118,6 +118,10 @@ def test_validation_codes(fmx):
     assert fmx.fmx_get_option(h, fmx.FMX_OPT_SELFTEST_LOST_ARRIVAL) == 0
     assert fmx.fmx_get_option(h, fmx.FMX_OPT_RESIDENT_CLUSTERS) == 0  # no launch yet
     assert fmx.fmx_set_option(h, fmx.FMX_OPT_RESIDENT_CLUSTERS, 2) == fmx.FMX_EINVAL  # read only
+    assert fmx.fmx_get_option(h, fmx.FMX_OPT_SEGMENT_ROWS) == 0  # automatic
+    assert fmx.fmx_set_option(h, fmx.FMX_OPT_SEGMENT_ROWS, -1) == fmx.FMX_EINVAL
+    assert fmx.fmx_set_option(h, fmx.FMX_OPT_SEGMENT_ROWS, 64) == fmx.FMX_OK
+    assert fmx.fmx_get_option(h, fmx.FMX_OPT_SEGMENT_ROWS) == 64
     fmx.fmx_destroy(h)
     # the FMA-rate measurement refuses bad arguments before any device work
     out = ctypes.c_double(0.0)
