@@ -382,9 +382,9 @@ fmx_status fmx_batch_tiles(const fmx_batch *b, int *wide, int *narrow, int *sing
  * not bound, i out of range). */
 int fmx_batch_grid_width(const fmx_batch *b, int i);
 
-/* Autotuner: times every pair of tile rule (1, then 0) and row extent
- * (automatic, 1024, 512, 256, 128, 64, 32) over `trial_steps` graph-replayed
- * steps with CUDA events, keeps the fastest pair and returns its row extent
+/* Autotuner: times every pair of tile rule (2, 1, then 0) and row extent
+ * (automatic, 1024, 512, 384, 256, 192, 128, 96, 64, 32) over `trial_steps`
+ * graph-replayed steps with CUDA events, keeps the fastest pair and returns its row extent
  * in *chosen (0 = automatic; chosen may be NULL; fmx_batch_tiles reports
  * both).  The choice is cached in the process by the batch's signature (m,
  * filter passes, current, every grid's size): a later batch of the same grids

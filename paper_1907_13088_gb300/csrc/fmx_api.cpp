@@ -2023,12 +2023,12 @@ fmx_status fmx_batch_tune(fmx_batch *b, int trial_steps, int *chosen) {
             return fmx_batch_set_rows(b, it->second.first);
         }
     }
-    // tile rule (narrow tiles where they compute fewer columns, or wide tiles
-    // only) x rows per segment (automatic, then fixed heights)
-    const int rule[] = {1, 0};
-    const int cand[] = {0, 1024, 512, 256, 128, 64, 32};
+    // tile rule (narrow tiles everywhere, where they compute fewer columns,
+    // or wide tiles only) x rows per segment (automatic, then fixed heights)
+    const int rule[] = {2, 1, 0};
+    const int cand[] = {0, 1024, 512, 384, 256, 192, 128, 96, 64, 32};
     float best = 1e30f;
-    int best_rows = 0, best_rule = 1;
+    int best_rows = 0, best_rule = 2;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return fail(FMX_ECUDA, "cudaEventCreate");

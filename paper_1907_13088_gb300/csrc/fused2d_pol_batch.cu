@@ -29,11 +29,12 @@ __global__ void __launch_bounds__(NT, 3)
 }
 
 // Batched step on the polarisation kernels: a persistent loop over tasks.
-// Task v < 2 nwide is the TE (v even) or TM (v odd) half of the wide tile
-// items[v/2] (the whole CTA, NT column pairs); the tasks after them take the
+// Task v < nwide is the TE half of the wide tile items[v] (the whole CTA, NT
+// column pairs) and task nwide + v its TM half; the tasks after them take the
 // narrow tiles (NT/2 column pairs) two at a time, one per half of the CTA,
-// both in the same polarisation.  One launch per step covers both halves of
-// every tile.
+// both in the same polarisation, again all TE pairs before all TM pairs (an
+// SM then mostly runs one tile body at a time).  One launch per step covers
+// both halves of every tile.
 template <int M, int P, bool HJ, int NT>
 __global__ void __launch_bounds__(NT, 3)
     k_pol2d_batch(const BatchGrid *__restrict__ grids, const BatchItem *__restrict__ items, int nwide, int nnarrow,
@@ -46,7 +47,10 @@ __global__ void __launch_bounds__(NT, 3)
         __syncthreads();  // both halves are done with the previous task's shared memory
         const bool narrow = v >= 2 * nwide;
         const int half = narrow ? (int)threadIdx.x / NH : 0;
-        const int it = narrow ? nwide + 2 * ((v - 2 * nwide) >> 1) + half : v >> 1;
+        // the TE halves of a kind of tile before its TM halves
+        const int vk = narrow ? v - 2 * nwide : v, nk = narrow ? npair : nwide;
+        const int tm = vk >= nk, k = vk - tm * nk;
+        const int it = narrow ? nwide + 2 * k + half : k;
         if (narrow && it >= nwide + nnarrow) continue;  // the odd last narrow tile has one half idle
         const BatchItem w = items[it];
         const BatchGrid &G = grids[w.grid];
@@ -67,10 +71,10 @@ __global__ void __launch_bounds__(NT, 3)
             const int xs = w.strip * G.W - PolGeom<M, P, HJ>::HC;
             const bool seam = (g.nx & 1) && !(xs >= 0 && xs + 2 * NT <= g.nx);
             if (!seam) {
-                if (v & 1) pol_tile<TM, M, P, HJ, NT>(a, g, c, G.W, G.L, w.strip, w.seg, sm);
+                if (tm) pol_tile<TM, M, P, HJ, NT>(a, g, c, G.W, G.L, w.strip, w.seg, sm);
                 else pol_tile<TE, M, P, HJ, NT>(a, g, c, G.W, G.L, w.strip, w.seg, sm);
             } else {
-                if (v & 1) pol_tile<TM, M, P, HJ, NT, true>(a, g, c, G.W, G.L, w.strip, w.seg, sm);
+                if (tm) pol_tile<TM, M, P, HJ, NT, true>(a, g, c, G.W, G.L, w.strip, w.seg, sm);
                 else pol_tile<TE, M, P, HJ, NT, true>(a, g, c, G.W, G.L, w.strip, w.seg, sm);
             }
         } else {
@@ -78,10 +82,10 @@ __global__ void __launch_bounds__(NT, 3)
             const int xs = w.strip * G.W - PolGeom<M, P, HJ>::HC;
             const bool seam = (g.nx & 1) && !(xs >= 0 && xs + 2 * NH <= g.nx);
             if (!seam) {
-                if (v & 1) pol_tile<TM, M, P, HJ, NH, false, true>(a, g, c, G.W, G.L, w.strip, w.seg, smh, half);
+                if (tm) pol_tile<TM, M, P, HJ, NH, false, true>(a, g, c, G.W, G.L, w.strip, w.seg, smh, half);
                 else pol_tile<TE, M, P, HJ, NH, false, true>(a, g, c, G.W, G.L, w.strip, w.seg, smh, half);
             } else {
-                if (v & 1) pol_tile<TM, M, P, HJ, NH, true, true>(a, g, c, G.W, G.L, w.strip, w.seg, smh, half);
+                if (tm) pol_tile<TM, M, P, HJ, NH, true, true>(a, g, c, G.W, G.L, w.strip, w.seg, smh, half);
                 else pol_tile<TE, M, P, HJ, NH, true, true>(a, g, c, G.W, G.L, w.strip, w.seg, smh, half);
             }
         }

@@ -96,7 +96,8 @@ def test_batch_tile_rows_do_not_change_results(fmx):
 def test_batch_tune_then_step(fmx):
     b = fmx.Batch(SHAPES, COURANT, m=4)
     chosen = b.tune(trial_steps=4)
-    assert chosen in (0, 1024, 512, 256, 128, 64, 32)
+    assert chosen in (0, 1024, 512, 384, 256, 192, 128, 96, 64, 32)
+    assert b.tiles()["narrow_rule"] in (0, 1, 2)
     inputs = [_fields(sh, 1907080 + i) for i, sh in enumerate(SHAPES)]
     for i, (E, B) in enumerate(inputs):
         b.set_fields(i, E, B)
