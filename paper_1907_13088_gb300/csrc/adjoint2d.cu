@@ -65,6 +65,7 @@ struct AdjSmem {
 template <int POL>
 struct AdjPrefetch {
     static constexpr int PE = POL == TM ? 4 : 2, PB = POL == TM ? 4 : 2, PF = POL == TM ? 4 : 2;
+    static constexpr int L1 = 2;  // rows beyond those whose Ebar, Bbar lines go to L1 (Adj2dArgs::l1pf)
 };
 
 template <int POL, int M, int P, bool HJB, int NT>
@@ -137,6 +138,9 @@ __global__ void __launch_bounds__(NT, 3)
         o += pitch;
         if (o >= plane) o -= plane;
     };
+    // L1 prefetch of the rows AdjPrefetch::L1 beyond the register loads
+    int le = row_off(r0 + AdjPrefetch<POL>::PE + AdjPrefetch<POL>::L1),
+        lb = row_off(r0 + 2 + AdjPrefetch<POL>::PB + AdjPrefetch<POL>::L1);
 
     const f2 z2 = mk(0.f, 0.f);
     f2 win[M > 0 ? M : 1][NC][3];
@@ -202,6 +206,14 @@ __global__ void __launch_bounds__(NT, 3)
             ldE(u % PE);
             ldB(u % PB);
             ldF(u % PFD);
+            if (a.l1pf) {
+                prefetch_l1(inE0 + le);
+                if (POL == TE) prefetch_l1(inE1 + le);
+                prefetch_l1(inB0 + lb);
+                if (POL == TM) prefetch_l1(inB1 + lb);
+                adv(le);
+                adv(lb);
+            }
             const int rhoM = r - 2 * M, rhoF = rhoM - 1;
             // u ring row of row r - k (u, k compile-time; b0 in {0, 4, 8})
             auto dprow = [&](int k) {
@@ -494,12 +506,14 @@ int launch_adjoint2d(const Geo &g, const Coef<float> &c, const Adj2dArgs<float> 
     k.ay = b(c.ay);
     k.axy = b(c.axy);
     k.bxy = b(c.bxy);
+    Adj2dArgs<float> a2 = a;
+    a2.l1pf = fused2d_l1_prefetch(g) ? 1 : 0;
     switch (a.m) {
-        case 0: return adj_p<0>(g, k, a, s, a.passes);
-        case 1: return adj_p<1>(g, k, a, s, a.passes);
-        case 2: return adj_p<2>(g, k, a, s, a.passes);
-        case 3: return adj_p<3>(g, k, a, s, a.passes);
-        case 4: return adj_p<4>(g, k, a, s, a.passes);
+        case 0: return adj_p<0>(g, k, a2, s, a.passes);
+        case 1: return adj_p<1>(g, k, a2, s, a.passes);
+        case 2: return adj_p<2>(g, k, a2, s, a.passes);
+        case 3: return adj_p<3>(g, k, a2, s, a.passes);
+        case 4: return adj_p<4>(g, k, a2, s, a.passes);
     }
     return -1;
 }

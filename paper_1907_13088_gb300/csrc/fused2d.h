@@ -64,7 +64,13 @@ struct Adj2dArgs {
     T *Jbo[3];       // dL/dj^{n+1/2} per component, or nullptr
     int m;           // sweeps
     int passes;      // binomial passes of the current filter
+    int l1pf;        // prefetch input rows into L1 (set by the launcher)
 };
+// Whether the 2D TE/TM kernels prefetch their input rows into L1: when a
+// step's algorithmic bytes (60 per cell) exceed 1.5 times the L2 cache, so
+// that the rows come from HBM (4096^2, m = 4, p = 3: +11%); below, with the
+// fields in L2, the prefetches only cost issue slots (1024^2: -23%).
+bool fused2d_l1_prefetch(const Geo &g);
 // even nx, 32-bit element offsets; m <= 4, passes <= 3
 bool adjoint2d_supported(const Geo &g, int m, int passes);
 int launch_adjoint2d(const Geo &g, const Coef<float> &c, const Adj2dArgs<float> &a, cudaStream_t s, int seg_rows = 0);

@@ -20,14 +20,17 @@ using pol2d::PolGeom;
 using pol2d::pol_tile;
 
 // rows per segment asked for by the caller of the current launch (0:
-// automatic, see PolLauncher::shape)
+// automatic, see PolLauncher::shape), and whether its tiles prefetch their
+// input rows into L1 (fused2d_l1_prefetch)
 thread_local int t_rows = 0;
+thread_local bool t_l1pf = false;
 
-template <int POL, int M, int P, bool HJ, int NT>
+template <int POL, int M, int P, bool HJ, int NT, bool L1PF>
 __global__ void __launch_bounds__(NT, 3)
     k_pol2d(Fused2dArgs<float> a, Geo g, Coef2 c, int W, int L, int nstrip) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    pol_tile<POL, M, P, HJ, NT>(a, g, c, W, L, blockIdx.x % nstrip, blockIdx.x / nstrip, reinterpret_cast<float *>(smraw));
+    pol_tile<POL, M, P, HJ, NT, false, false, L1PF>(a, g, c, W, L, blockIdx.x % nstrip, blockIdx.x / nstrip,
+                                                    reinterpret_cast<float *>(smraw));
 }
 
 template <int POL, int M, int P, bool HJ>
@@ -37,8 +40,10 @@ struct PolLauncher {
     static int blocks_per_sm() {
         static int b = -1;
         if (b < 0) {
-            auto k = k_pol2d<POL, M, P, HJ, NT>;
+            auto k = k_pol2d<POL, M, P, HJ, NT, false>;
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes());
+            cudaFuncSetAttribute(k_pol2d<POL, M, P, HJ, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_bytes());
             int n = 0;
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, NT, smem_bytes()) != cudaSuccess || n < 1) n = 1;
             b = n;
@@ -76,9 +81,12 @@ struct PolLauncher {
     }
     static void run(const Geo &g, const Coef2 &c, const Fused2dArgs<float> &a, cudaStream_t s) {
         const Fused2dShape sh = shape(g);
-        if (g.nx % 2 == 0)
-            k_pol2d<POL, M, P, HJ, NT><<<sh.strips * sh.segments, NT, smem_bytes(), s>>>(a, g, c, sh.width, sh.rows,
-                                                                                        sh.strips);
+        if (g.nx % 2 == 0 && t_l1pf)
+            k_pol2d<POL, M, P, HJ, NT, true><<<sh.strips * sh.segments, NT, smem_bytes(), s>>>(a, g, c, sh.width, sh.rows,
+                                                                                              sh.strips);
+        else if (g.nx % 2 == 0)
+            k_pol2d<POL, M, P, HJ, NT, false><<<sh.strips * sh.segments, NT, smem_bytes(), s>>>(a, g, c, sh.width,
+                                                                                               sh.rows, sh.strips);
         else
             pol2d::launch_odd<POL, M, P, HJ>(g, c, a, sh.width, sh.rows, sh.strips, sh.strips * sh.segments, s);
     }
@@ -137,6 +145,16 @@ Coef2 make_coef2(const Coef<float> &c, int passes) { return pol2d::coef2_of(c, p
 // time)
 bool fused2d_pol_supported(const Geo &g) { return (int64_t)g.ny * g.pitch < ((int64_t)1 << 31); }
 
+bool fused2d_l1_prefetch(const Geo &g) {
+    static long long l2 = -1;
+    if (l2 < 0) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        l2 = cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev) == cudaSuccess && v > 0 ? v : (1LL << 27);
+    }
+    return 60.0 * (double)g.nx * (double)g.ny > 1.5 * (double)l2;
+}
+
 int launch_fused2d_pol(const Geo &g, const Coef<float> &c, const Fused2dArgs<float> &a, cudaStream_t s,
                        cudaEvent_t *ev, cudaStream_t s_tm, int seg_rows) {
     const bool hj = a.J[0] != nullptr;
@@ -145,10 +163,12 @@ int launch_fused2d_pol(const Geo &g, const Coef<float> &c, const Fused2dArgs<flo
     t_ev = ev;
     t_tm = s_tm;
     t_rows = seg_rows;
+    t_l1pf = fused2d_l1_prefetch(g);
     const int n = pol_dispatch(g, make_coef2(c, p), a, s, a.m, hj, p, nullptr);
     t_ev = nullptr;
     t_tm = nullptr;
     t_rows = 0;
+    t_l1pf = false;
     return n;
 }
 

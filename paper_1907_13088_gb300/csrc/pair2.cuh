@@ -53,5 +53,9 @@ __device__ __forceinline__ f2 binom_taps(const f2 *v) {
 
 enum { TE = 0, TM = 1 };
 
+// a hint: the line holding *p is fetched into L1 ahead of a later load of it
+// (no register holds it; p must be an address the kernel may load)
+__device__ __forceinline__ void prefetch_l1(const float *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
 }  // namespace pair2
 }  // namespace fmx

@@ -47,6 +47,10 @@ template <int POL>
 struct PolPrefetch {
     static constexpr int PJ = POL == TM ? 4 : 2, PB = POL == TM ? 4 : 2, PE = POL == TM ? 4 : 2,
                          PF = POL == TM ? 4 : 2;
+    // rows beyond those register loads whose j, B and E lines are prefetched
+    // into L1 by the L1PF tiles (no register holds them).  4096^2, m = 4, p = 3: 65.3 Gcell/s without, 72.1 with 2
+    // rows (1 to 4 rows, for TE and TM apart, all within 71.6-72.1; 8 rows 71.0)
+    static constexpr int L1 = 2;
 };
 
 template <int M, int P, bool HJ>
@@ -84,8 +88,10 @@ struct PolSmem {
 // grid, in the shared memory `sm` (PolSmem layout).  HALF: the tile is run by
 // one half of the CTA (threads half * NT .. half * NT + NT - 1), which
 // synchronises on its own named barrier 1 + half, so that a CTA can carry
-// two independent narrow tiles; otherwise the whole CTA runs it.
-template <int POL, int M, int P, bool HJ, int NT, bool SEAM = false, bool HALF = false>
+// two independent narrow tiles; otherwise the whole CTA runs it.  L1PF: the
+// input rows are also prefetched into L1 PolPrefetch::L1 rows beyond the
+// register loads (for grids whose rows come from HBM).
+template <int POL, int M, int P, bool HJ, int NT, bool SEAM = false, bool HALF = false, bool L1PF = false>
 __device__ __forceinline__ void pol_tile(const Fused2dArgs<float> &a, const Geo &g, const Coef2 &c, int W, int L,
                                          int strip, int seg, float *sm, int half = 0) {
     using G = PolGeom<M, P, HJ>;
@@ -169,6 +175,14 @@ __device__ __forceinline__ void pol_tile(const Fused2dArgs<float> &a, const Geo 
         o += pitch;
         if (o >= plane) o -= plane;
     };
+    // L1 prefetch: the rows PolPrefetch::L1 beyond the register loads
+    constexpr int L1D = PolPrefetch<POL>::L1;
+    int lj = 0, lb = 0, le = 0;
+    if constexpr (L1PF) {
+        lj = row_off(r0 + 1 + P + PolPrefetch<POL>::PJ + L1D);
+        lb = row_off(r0 + 2 + PolPrefetch<POL>::PB + L1D);
+        le = row_off(r0 - 2 * M + PolPrefetch<POL>::PE + L1D);
+    }
 
     // register state (pairs)
     f2 jw[NC][TJ];
@@ -274,6 +288,19 @@ __device__ __forceinline__ void pol_tile(const Fused2dArgs<float> &a, const Geo 
             ldB(u % PB);
             ldE(u % PE);
             ldF(u % PFD);
+            if constexpr (L1PF && L1D > 0) {
+                if (HJ) {
+                    prefetch_l1(inJ0 + lj);
+                    if (POL == TE) prefetch_l1(inJ1 + lj);
+                }
+                prefetch_l1(inB0 + lb);
+                if (POL == TM) prefetch_l1(inB1 + lb);
+                prefetch_l1(inE0 + le);
+                if (POL == TE) prefetch_l1(inE1 + le);
+                adv(lj);
+                adv(lb);
+                adv(le);
+            }
             const int rhoM = r - 2 * M, rhoF = rhoM - 1;
             // dE' ring row of row r - k (u, k compile-time; b0 a multiple of 4)
             auto dprow = [&](int k) {
