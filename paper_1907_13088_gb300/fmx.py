@@ -232,6 +232,68 @@ def make_params(shape, d=(1.0, 1.0, 1.0), c=1.0, dt=0.0, courant=0.5, precision=
     return p
 
 
+def _is_tensor(a) -> bool:
+    return type(a).__module__.startswith("torch") and hasattr(a, "data_ptr")
+
+
+def component_ptr(a, cells, np_dtype, torch_dtype=None, dev_index=None, out=False):
+    """Checks one field component before its pointer goes to the library and
+    returns (pointer, keep-alive object, FMX_HOST or FMX_DEVICE).
+
+    The library copies exactly ``cells`` elements of the grid's precision per
+    component and trusts the pointer, so a short array, another dtype, a
+    strided view or a tensor on another device would make it read or write
+    past the buffer.  A numpy input is converted (a contiguous copy of the
+    grid's dtype); a numpy output must already be a C-contiguous, writeable
+    array of that dtype.  A torch tensor must be a CUDA tensor of the grid's
+    dtype on device ``dev_index`` (None: any CUDA device), contiguous when it
+    receives data; an input is made contiguous.  Raises TypeError or
+    ValueError; nothing is copied here."""
+    if isinstance(a, np.ndarray):
+        if out:
+            if a.dtype != np.dtype(np_dtype) or not a.flags.c_contiguous or not a.flags.writeable:
+                raise TypeError(f"host output must be a writeable C-contiguous {np.dtype(np_dtype)} array "
+                                f"(got {a.dtype}, contiguous={a.flags.c_contiguous}, writeable={a.flags.writeable})")
+        else:
+            a = np.ascontiguousarray(a, dtype=np_dtype)
+        if a.size != cells:
+            raise ValueError(f"a field component has {a.size} elements, the grid {cells}")
+        return a.ctypes.data, a, FMX_HOST
+    if _is_tensor(a):
+        if not a.is_cuda:
+            raise TypeError("torch tensors must be CUDA tensors on the grid's device (pass numpy arrays for host data)")
+        if dev_index is not None and a.device.index != dev_index:
+            raise ValueError(f"tensor on cuda:{a.device.index}, the grid on cuda:{dev_index}")
+        if torch_dtype is not None and a.dtype != torch_dtype:
+            raise TypeError(f"tensor of {a.dtype}, the grid stores {torch_dtype}")
+        if out and not a.is_contiguous():
+            raise TypeError("an output tensor must be contiguous")
+        if a.numel() != cells:
+            raise ValueError(f"a field component has {a.numel()} elements, the grid {cells}")
+        a = a.contiguous()
+        return a.data_ptr(), a, FMX_DEVICE
+    raise TypeError(f"a field component must be a numpy array or a CUDA tensor (got {type(a).__name__})")
+
+
+def component_ptrs(arrays, cells, np_dtype, torch_dtype=None, dev_index=None, out=False):
+    """component_ptr over a list (None entries stay NULL): returns (ctypes
+    pointer array, keep-alive list, FMX_HOST or FMX_DEVICE).  Host and device
+    components cannot be mixed in one call."""
+    ptrs = (ctypes.c_void_p * len(arrays))()
+    keep, where = [], set()
+    for i, a in enumerate(arrays):
+        if a is None:
+            ptrs[i] = None
+            continue
+        p, k, w = component_ptr(a, cells, np_dtype, torch_dtype, dev_index, out)
+        ptrs[i] = p
+        keep.append(k)
+        where.add(w)
+    if len(where) > 1:
+        raise TypeError("host arrays and device tensors cannot be mixed in one call")
+    return ptrs, keep, (where.pop() if where else FMX_HOST)
+
+
 class Grid:
     """A field-advance grid whose device buffers are PyTorch tensors.
 
@@ -283,6 +345,8 @@ class Grid:
         check(fmx_bind(self.handle, ctypes.byref(b)), "fmx_bind")
         nx, ny, nz = self.shape + (1,) * (3 - len(self.shape))
         self.array_shape = (3, nz, ny, nx)
+        self.cells = nx * ny * nz
+        self._dev_index = self._slab.device.index
 
     # -- lifetime --------------------------------------------------------
     def close(self):
@@ -297,40 +361,30 @@ class Grid:
             pass
 
     # -- copies ----------------------------------------------------------
-    def _ptr_array(self, arrays):
-        keep = []
-        ptrs = (ctypes.c_void_p * len(arrays))()
-        for i, a in enumerate(arrays):
-            if a is None:
-                ptrs[i] = None
-            elif isinstance(a, np.ndarray):
-                a = np.ascontiguousarray(a, dtype=self.np_dtype)
-                keep.append(a)
-                ptrs[i] = a.ctypes.data
-            else:
-                a = a.contiguous()
-                keep.append(a)
-                ptrs[i] = a.data_ptr()
-        return ptrs, keep
+    def _ptr_array(self, arrays, out=False):
+        """Checked pointers of field components (component_ptrs with this
+        grid's size, dtype and device)."""
+        return component_ptrs(arrays, self.cells, self.np_dtype, self.dtype, self._dev_index, out)
 
     def set_fields(self, E=None, B=None):
         arrs = [None] * 6
         mask = 0
-        where = FMX_HOST
         for k, F in enumerate((E, B)):
             if F is None:
                 continue
+            if len(F) != 3:
+                raise ValueError(f"{'EB'[k]} must have 3 components (got {len(F)})")
             for c in range(3):
                 arrs[3 * k + c] = F[c]
                 mask |= 1 << (3 * k + c)
-            where = FMX_HOST if isinstance(F, np.ndarray) else FMX_DEVICE
-        ptrs, keep = self._ptr_array(arrs)
+        ptrs, keep, where = self._ptr_array(arrs)
         check(fmx_set_fields(self.handle, mask, ptrs, where), "fmx_set_fields")
         del keep
 
     def set_current(self, J):
-        ptrs, keep = self._ptr_array([J[0], J[1], J[2]])
-        where = FMX_HOST if isinstance(J, np.ndarray) else FMX_DEVICE
+        if len(J) != 3:
+            raise ValueError(f"J must have 3 components (got {len(J)})")
+        ptrs, keep, where = self._ptr_array([J[0], J[1], J[2]])
         check(fmx_set_current(self.handle, ptrs, where), "fmx_set_current")
         del keep
 
@@ -346,15 +400,17 @@ class Grid:
         given device tensors ``out`` of that shape.  Returns E, B, J arrays of
         shape (3, nz, ny, nx) (None where not requested)."""
         nz, ny, nx = self.array_shape[1:]
-        if out is None:
-            host = host_out if host_out is not None else np.zeros((9, nz, ny, nx), dtype=self.np_dtype)
-            ptrs = (ctypes.c_void_p * 9)(*[host[c].ctypes.data if mask & (1 << c) else None for c in range(9)])
-            check(fmx_get_fields(self.handle, mask, ptrs, FMX_HOST), "fmx_get_fields")
-            res = host
-        else:
-            ptrs = (ctypes.c_void_p * 9)(*[out[c].data_ptr() if mask & (1 << c) else None for c in range(9)])
-            check(fmx_get_fields(self.handle, mask, ptrs, FMX_DEVICE), "fmx_get_fields")
-            res = out
+        res = out if out is not None else (host_out if host_out is not None else
+                                           np.zeros((9, nz, ny, nx), dtype=self.np_dtype))
+        if len(res) != 9:
+            raise ValueError(f"the output holds {len(res)} components, not 9 (E, B, J)")
+        if out is not None and not _is_tensor(out):
+            raise TypeError("out must be a CUDA tensor (host arrays go to host_out)")
+        if out is None and not isinstance(res, np.ndarray):
+            raise TypeError("host_out must be a numpy array")
+        ptrs, keep, where = self._ptr_array([res[c] if mask & (1 << c) else None for c in range(9)], out=True)
+        check(fmx_get_fields(self.handle, mask, ptrs, FMX_DEVICE if out is not None else FMX_HOST), "fmx_get_fields")
+        del keep
         E = res[0:3] if mask & FMX_E else None
         B = res[3:6] if mask & FMX_B else None
         J = res[6:9] if mask & FMX_J else None
@@ -378,6 +434,18 @@ class Grid:
         recs = (fmx_host_step * len(steps))()
         keep = []
         for i, (inp, out) in enumerate(steps):
+            # the library reads and writes these arrays in place: no conversion
+            if not isinstance(inp, np.ndarray) or len(inp) not in (6, 9):
+                raise ValueError(f"step {i}: inputs must be a host array of 6 or 9 components")
+            if out is not None and (not isinstance(out, np.ndarray) or len(out) != 6):
+                raise ValueError(f"step {i}: outputs must be a host array of 6 components or None")
+            for arr in (inp,) + ((out,) if out is not None else ()):
+                if arr.dtype != np.dtype(self.np_dtype) or not arr.flags.c_contiguous:
+                    raise TypeError(f"step {i}: host arrays must be C-contiguous {np.dtype(self.np_dtype)}")
+                if arr[0].size != self.cells:
+                    raise ValueError(f"step {i}: {arr[0].size} elements per component, the grid {self.cells}")
+            if out is not None and not out.flags.writeable:
+                raise TypeError(f"step {i}: the output array is read-only")
             for c in range(9):
                 recs[i].inp[c] = inp[c].ctypes.data if c < len(inp) else None
             for c in range(6):
@@ -518,7 +586,12 @@ class Batch:
             pass
 
     def set_fields(self, i, E, B):
+        nx, ny = self.shapes[i]
+        if len(E) != 3 or len(B) != 3:
+            raise ValueError("E and B must have 3 components each")
         keep = [np.ascontiguousarray(F[c], dtype=np.float32) for F in (E, B) for c in range(3)]
+        if any(k.size != nx * ny for k in keep):
+            raise ValueError(f"grid {i} has {nx * ny} cells per component")
         ptrs = (ctypes.c_void_p * 6)(*[k.ctypes.data for k in keep])
         check(fmx_batch_set_fields(self.handle, i, FMX_E | FMX_B, ptrs, FMX_HOST), "fmx_batch_set_fields")
 
