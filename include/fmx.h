@@ -102,7 +102,8 @@ enum {
 
 typedef struct {
     int dims;            /* active axes: 1 (x), 2 (x, y) or 3 (x, y, z)                  */
-    int64_t n[3];        /* cells per axis, >= 1; inactive axes must be 1               */
+    int64_t n[3];        /* cells per axis, 1 .. 2^30; inactive axes must be 1; one field
+                            array (pitch * n[1] * n[2] elements) at most 2^40 bytes   */
     double d[3];         /* cell sizes (dx, dy, dz) > 0                                 */
     double c;            /* speed of light > 0                                          */
     double dt;           /* time step; if <= 0, dt = courant * dt_CFL                   */

@@ -186,6 +186,12 @@ fmx_status validate(const fmx_params *p, double *dt_out, int *warn) {
     const int64_t q = (int64_t)(16 / elem_size(p->precision));
     if (p->pitch != 0 && (p->pitch < p->n[0] || p->pitch % q != 0))
         return fail(FMX_EINVAL, "pitch must be >= n[0] and a multiple of 16 bytes");
+    // every size below (cells, bytes per array, workspaces) is a product of
+    // the extents; bounding one array at 2^40 bytes keeps them all far from
+    // int64 overflow (the extents alone allow 2^90 cells)
+    const double array_bytes = (double)pitch_of(p) * (double)p->n[1] * (double)p->n[2] * (double)elem_size(p->precision);
+    if (array_bytes > 1099511627776.0)
+        return fail(FMX_EINVAL, "one field array would take %.3g bytes (limit 2^40)", array_bytes);
     const double cfl = dt_cfl(p);
     double dt = p->dt;
     if (!(dt > 0.0)) {

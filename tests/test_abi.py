@@ -83,6 +83,12 @@ def test_validation_codes(fmx):
     p.n[2] = 3
     assert fmx.create_status(p)[0] == fmx.FMX_EINVAL
     assert fmx.create_status(fmx.make_params((16, 16), pitch=17))[0] == fmx.FMX_EINVAL
+    # extents whose product would overflow the size arithmetic: one field array is capped at 2^40 bytes
+    assert fmx.create_status(fmx.make_params((1 << 30, 1 << 30, 1 << 30)))[0] == fmx.FMX_EINVAL
+    assert fmx.fmx_field_bytes(__import__("ctypes").byref(fmx.make_params((1 << 30, 1 << 30, 1 << 30)))) == 0
+    assert fmx.create_status(fmx.make_params((8192, 8192, 8192)))[0] == fmx.FMX_EINVAL  # 2^41 bytes in FP32
+    assert fmx.create_status(fmx.make_params((8192, 8192, 4096)))[0] == fmx.FMX_OK  # 2^40 bytes
+    assert fmx.create_status(fmx.make_params((1 << 30, 1 << 10), precision=1))[0] == fmx.FMX_EINVAL
     assert fmx.create_status(fmx.make_params((16, 16), iter_mode=1, tol=0.0))[0] == fmx.FMX_EINVAL
     assert fmx.create_status(fmx.make_params((16, 16), m=-1))[0] == fmx.FMX_EINVAL
     # the fused engine covers 2D fixed sweeps only
