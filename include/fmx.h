@@ -174,7 +174,8 @@ fmx_status fmx_bind(fmx_grid *g, const fmx_buffers *b);
 /* Copies the components in `mask` (FMX_E/FMX_B bits) from src[c] (c = 0..5:
  * Ex, Ey, Ez, Bx, By, Bz; entries outside mask ignored) into the current
  * state set.  Sources are dense (pitch = n[0]) arrays of the grid's
- * precision; `where` says whether they are host or device memory.  E is
+ * precision; `where` (FMX_HOST or FMX_DEVICE; any other value is
+ * FMX_EINVAL) says whether they are host or device memory.  E is
  * read as E^n and B as B^{n+1/2}.  Host copies complete before return;
  * device copies are enqueued on the stream.  Errors: FMX_EINVAL,
  * FMX_ESTATE (not bound), FMX_ECUDA. */
@@ -219,7 +220,8 @@ fmx_status fmx_filter(fmx_grid *g, unsigned mask, int passes);
 
 /* Copies the components in mask (FMX_E/FMX_B/FMX_J bits; dst indexed
  * 0..8 as Ex..Bz, Jx, Jy, Jz) out of the current state into dense arrays at
- * dst[c].  Synchronises the stream.  Errors: FMX_EINVAL, FMX_ESTATE,
+ * dst[c], host or device memory as `where` says (FMX_HOST or FMX_DEVICE).
+ * Synchronises the stream.  Errors: FMX_EINVAL, FMX_ESTATE,
  * FMX_ECUDA, FMX_ETIMEOUT (a latched device status). */
 fmx_status fmx_get_fields(fmx_grid *g, unsigned mask, void *const *dst, int where);
 
@@ -350,7 +352,7 @@ fmx_status fmx_batch_bind(fmx_batch *b, const fmx_buffers *bufs, void *work, siz
 /* Copy grid i's components in or out of its current state set (as
  * fmx_set_fields / fmx_get_fields; get synchronises).  mask: FMX_E and FMX_B
  * bits only; every component the mask names needs a pointer.  Errors:
- * FMX_EINVAL (bad index, mask or NULL pointer), FMX_ESTATE (not bound),
+ * FMX_EINVAL (bad index, mask, `where` or NULL pointer), FMX_ESTATE (not bound),
  * FMX_ECUDA. */
 fmx_status fmx_batch_set_fields(fmx_batch *b, int i, unsigned mask, const void *const *src, int where);
 fmx_status fmx_batch_get_fields(fmx_batch *b, int i, unsigned mask, void *const *dst, int where);

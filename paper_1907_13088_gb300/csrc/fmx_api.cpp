@@ -965,6 +965,7 @@ fmx_status fmx_bind(fmx_grid *g, const fmx_buffers *b) {
 
 fmx_status fmx_set_fields(fmx_grid *g, unsigned mask, const void *const *src, int where) {
     if (!g || !src) return fail(FMX_EINVAL, "NULL argument");
+    if (where != FMX_HOST && where != FMX_DEVICE) return fail(FMX_EINVAL, "where must be FMX_HOST or FMX_DEVICE");
     if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
     if (mask & ~(unsigned)(FMX_E | FMX_B)) return fail(FMX_EINVAL, "mask holds bits other than E and B");
     const size_t sp = (size_t)g->geo.nx * g->elem, dp = (size_t)g->geo.pitch * g->elem;
@@ -996,6 +997,7 @@ fmx_status fmx_set_current_profile(fmx_grid *g, const double *table, int len) {
 
 fmx_status fmx_set_current(fmx_grid *g, const void *const *src, int where) {
     if (!g || !src) return fail(FMX_EINVAL, "NULL argument");
+    if (where != FMX_HOST && where != FMX_DEVICE) return fail(FMX_EINVAL, "where must be FMX_HOST or FMX_DEVICE");
     if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
     if (!g->buf.J[0]) return fail(FMX_ESTATE, "no J buffers bound");
     const size_t sp = (size_t)g->geo.nx * g->elem, dp = (size_t)g->geo.pitch * g->elem;
@@ -1049,10 +1051,10 @@ fmx_status fmx_filter(fmx_grid *g, unsigned mask, int passes) {
 
 fmx_status fmx_get_fields(fmx_grid *g, unsigned mask, void *const *dst, int where) {
     if (!g || !dst) return fail(FMX_EINVAL, "NULL argument");
+    if (where != FMX_HOST && where != FMX_DEVICE) return fail(FMX_EINVAL, "where must be FMX_HOST or FMX_DEVICE");
     if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
     if (mask & ~(unsigned)(FMX_E | FMX_B | FMX_J)) return fail(FMX_EINVAL, "bad mask");
     if ((mask & FMX_J) && !g->buf.J[0]) return fail(FMX_ESTATE, "no J buffers bound");
-    (void)where;
     const size_t dp = (size_t)g->geo.nx * g->elem, sp = (size_t)g->geo.pitch * g->elem;
     for (int c = 0; c < 9; ++c) {
         if (!(mask & (1u << c))) continue;
@@ -1901,6 +1903,7 @@ fmx_status fmx_batch_bind(fmx_batch *b, const fmx_buffers *bufs, void *work, siz
 
 fmx_status fmx_batch_set_fields(fmx_batch *b, int i, unsigned mask, const void *const *src, int where) {
     if (!b || !src || i < 0 || i >= b->n) return fail(FMX_EINVAL, "bad arguments");
+    if (where != FMX_HOST && where != FMX_DEVICE) return fail(FMX_EINVAL, "where must be FMX_HOST or FMX_DEVICE");
     if (!b->bound) return fail(FMX_ESTATE, "batch not bound");
     if (mask & ~(unsigned)(FMX_E | FMX_B)) return fail(FMX_EINVAL, "mask holds bits other than E and B");
     const fmx::BatchGrid &G = b->grids[i];
@@ -1921,9 +1924,9 @@ fmx_status fmx_batch_set_fields(fmx_batch *b, int i, unsigned mask, const void *
 
 fmx_status fmx_batch_get_fields(fmx_batch *b, int i, unsigned mask, void *const *dst, int where) {
     if (!b || !dst || i < 0 || i >= b->n) return fail(FMX_EINVAL, "bad arguments");
+    if (where != FMX_HOST && where != FMX_DEVICE) return fail(FMX_EINVAL, "where must be FMX_HOST or FMX_DEVICE");
     if (!b->bound) return fail(FMX_ESTATE, "batch not bound");
     if (mask & ~(unsigned)(FMX_E | FMX_B)) return fail(FMX_EINVAL, "mask holds bits other than E and B");
-    (void)where;
     const fmx::BatchGrid &G = b->grids[i];
     const size_t dpch = (size_t)G.g.nx * 4, sp = (size_t)G.g.pitch * 4;
     for (int c = 0; c < 6; ++c) {

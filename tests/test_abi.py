@@ -106,6 +106,19 @@ def test_validation_codes(fmx):
     assert fmx.create_status(fmx.make_params((64, 64), filter_passes=1, filter_target=fmx.FMX_FILTER_FIELDS,
                                              engine=R))[0] == fmx.FMX_EUNSUPPORTED
     assert fmx.create_status(fmx.make_params((16, 16), engine=4))[0] == fmx.FMX_EINVAL
+    # the copy calls check `where` before anything else about the grid
+    import ctypes as _ct
+    h0 = _ct.c_void_p()
+    assert fmx.fmx_create(_ct.byref(fmx.make_params((16, 16))), _ct.byref(h0), None) == fmx.FMX_OK
+    ptrs = (_ct.c_void_p * 9)()
+    for where in (-1, 2, 7):
+        assert fmx.fmx_set_fields(h0, fmx.FMX_E, ptrs, where) == fmx.FMX_EINVAL
+        assert fmx.fmx_set_current(h0, ptrs, where) == fmx.FMX_EINVAL
+        assert fmx.fmx_get_fields(h0, fmx.FMX_E, ptrs, where) == fmx.FMX_EINVAL
+    for where in (fmx.FMX_HOST, fmx.FMX_DEVICE):  # valid: the next check is the unbound grid
+        assert fmx.fmx_set_fields(h0, fmx.FMX_E, ptrs, where) == fmx.FMX_ESTATE
+        assert fmx.fmx_get_fields(h0, fmx.FMX_E, ptrs, where) == fmx.FMX_ESTATE
+    fmx.fmx_destroy(h0)
     # per-grid kernel options (host only)
     import ctypes
     h = ctypes.c_void_p()
@@ -174,6 +187,8 @@ def test_batch_validation(fmx):
     assert fmx.fmx_batch_get_fields(h, 0, fmx.FMX_E, ptrs, fmx.FMX_HOST) == fmx.FMX_ESTATE
     assert fmx.fmx_batch_set_fields(h, 0, fmx.FMX_E, ptrs, fmx.FMX_HOST) == fmx.FMX_ESTATE
     assert fmx.fmx_batch_get_fields(h, 2, fmx.FMX_E, ptrs, fmx.FMX_HOST) == fmx.FMX_EINVAL  # no grid 2
+    assert fmx.fmx_batch_get_fields(h, 0, fmx.FMX_E, ptrs, 5) == fmx.FMX_EINVAL  # where
+    assert fmx.fmx_batch_set_fields(h, 0, fmx.FMX_E, ptrs, -1) == fmx.FMX_EINVAL
     # bind's argument checks come before any device work (the pointers are
     # never dereferenced on these paths)
     bufs = (fmx.fmx_buffers * 2)()
