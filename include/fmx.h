@@ -155,7 +155,11 @@ typedef struct fmx_grid fmx_grid;
  * *warnings receives FMX_WARN_* bits (may be NULL).
  * Errors: FMX_EINVAL (bad sizes, dims, precision, modes, pitch),
  * FMX_ECFL (dt > dt_CFL, Eq. dt_cfl_3d), FMX_EUNSUPPORTED (engine FUSED
- * requested for a case the fused kernel does not cover). */
+ * requested for a case the fused kernel does not cover; a grid that the
+ * staged engine would run with n[1] > 524280 or n[2] > 65535, the launch
+ * limits of its one-thread-per-cell kernels, which fmx_filter,
+ * fmx_diagnostics and fmx_adjoint_step share: those calls return
+ * FMX_EUNSUPPORTED for such a grid whatever its engine). */
 fmx_status fmx_create(const fmx_params *p, fmx_grid **out, int *warnings);
 
 /* Bytes of one field-component array: pitch * n[1] * n[2] * element size.

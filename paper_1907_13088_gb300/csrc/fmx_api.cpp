@@ -78,6 +78,14 @@ bool resident_supported(const fmx_params *p) {
     return true;
 }
 
+// The one-thread-per-cell kernels (staged engine, filter, diagnostics, staged
+// adjoint) launch (32, 8) blocks on a (n_x/32, n_y/8, n_z) grid, whose y and
+// z extents the hardware caps at 65535.
+bool cellwise_launch_ok(const fmx_params *p) { return (p->n[1] + 7) / 8 <= 65535 && p->n[2] <= 65535; }
+fmx_status cellwise_limit_fail(const char *what) {
+    return fail(FMX_EUNSUPPORTED, "%s: one-thread-per-cell kernels need n[1] <= 524280 and n[2] <= 65535", what);
+}
+
 // Which engine runs a step of this problem.
 int resolve_engine(const fmx_params *p) {
     const bool fusable = fmx::fused2d_supported(p);
@@ -209,6 +217,7 @@ fmx_status validate(const fmx_params *p, double *dt_out, int *warn) {
     if (resolve_engine(p) < 0)
         return fail(FMX_EUNSUPPORTED, "the %s engine does not cover this problem",
                     p->engine == FMX_ENGINE_FUSED ? "fused" : "resident");
+    if (resolve_engine(p) == FMX_ENGINE_STAGED && !cellwise_launch_ok(p)) return cellwise_limit_fail("staged engine");
     *dt_out = dt;
     if (warn) *warn = w;
     return FMX_OK;
@@ -794,6 +803,7 @@ template <typename T>
 fmx_status adjoint_impl(fmx_grid *g, void *const *Eb_, void *const *Bb_, void *const *jb_, void *work,
                         size_t work_bytes, unsigned jmask = 7u) {
     if (g->p.iter_mode != FMX_ITER_FIXED) return fail(FMX_EUNSUPPORTED, "the adjoint covers fixed m only");
+    if (!cellwise_launch_ok(&g->p)) return cellwise_limit_fail("adjoint step");
     if (g->p.filter_target == FMX_FILTER_FIELDS && g->p.filter_passes > 0)
         return fail(FMX_EUNSUPPORTED, "the adjoint does not cover field filtering");
     const size_t need = workspace_of(&g->p, FMX_ENGINE_STAGED);
@@ -1039,6 +1049,7 @@ fmx_status fmx_filter(fmx_grid *g, unsigned mask, int passes) {
     if (passes < 0) return fail(FMX_EINVAL, "passes < 0");
     if (mask & ~(unsigned)(FMX_E | FMX_B | FMX_J)) return fail(FMX_EINVAL, "bad mask");
     if ((mask & FMX_J) && !g->buf.J[0]) return fail(FMX_ESTATE, "no J buffers bound");
+    if (mask && passes > 0 && !cellwise_launch_ok(&g->p)) return cellwise_limit_fail("fmx_filter");
     for (int c = 0; c < 9; ++c) {
         if (!(mask & (1u << c))) continue;
         void *f = c < 3 ? g->buf.E[g->cur][c] : (c < 6 ? g->buf.B[g->cur][c - 3] : g->buf.J[c - 6]);
@@ -1069,6 +1080,7 @@ fmx_status fmx_get_fields(fmx_grid *g, unsigned mask, void *const *dst, int wher
 fmx_status fmx_diagnostics(fmx_grid *g, fmx_diag *out) {
     if (!g || !out) return fail(FMX_EINVAL, "NULL argument");
     if (!g->bound) return fail(FMX_ESTATE, "grid not bound");
+    if (!cellwise_launch_ok(&g->p)) return cellwise_limit_fail("fmx_diagnostics");
     double co[FMX_NCOEF];
     memcpy(co, g->co, sizeof(co));
     const fmx::Coef<double> c = make_coef<double>(co);

@@ -89,6 +89,14 @@ def test_validation_codes(fmx):
     assert fmx.create_status(fmx.make_params((8192, 8192, 8192)))[0] == fmx.FMX_EINVAL  # 2^41 bytes in FP32
     assert fmx.create_status(fmx.make_params((8192, 8192, 4096)))[0] == fmx.FMX_OK  # 2^40 bytes
     assert fmx.create_status(fmx.make_params((1 << 30, 1 << 10), precision=1))[0] == fmx.FMX_EINVAL
+    # launch limits of the one-thread-per-cell kernels: (n_x/32, n_y/8, n_z) blocks, y and z <= 65535
+    S = fmx.FMX_ENGINE_STAGED
+    assert fmx.create_status(fmx.make_params((4, 524280), engine=S))[0] == fmx.FMX_OK
+    assert fmx.create_status(fmx.make_params((4, 524281), engine=S))[0] == fmx.FMX_EUNSUPPORTED
+    assert fmx.create_status(fmx.make_params((4, 524281), iter_mode=1))[0] == fmx.FMX_EUNSUPPORTED  # AUTO -> staged
+    assert fmx.create_status(fmx.make_params((4, 524281), m=4))[0] == fmx.FMX_OK  # AUTO -> fused, 1D launch grid
+    assert fmx.create_status(fmx.make_params((2, 2, 65535), m=4))[0] == fmx.FMX_OK
+    assert fmx.create_status(fmx.make_params((2, 2, 65536), m=4))[0] == fmx.FMX_EUNSUPPORTED
     assert fmx.create_status(fmx.make_params((16, 16), iter_mode=1, tol=0.0))[0] == fmx.FMX_EINVAL
     assert fmx.create_status(fmx.make_params((16, 16), m=-1))[0] == fmx.FMX_EINVAL
     # the fused engine covers 2D fixed sweeps only
