@@ -131,11 +131,15 @@ def make_function():
             th = theta.detach().cpu().numpy().astype(np.float64)
             EN, BN = run.forward(th, E0.detach(), B0.detach())
             ctx.run, ctx.theta, ctx.recompute = run, th, recompute
+            ctx.theta_meta = (theta.dtype, theta.device)
             return EN, BN
 
         @staticmethod
         def backward(ctx, gE, gB):
             grad, gE0, gB0 = ctx.run.backward(ctx.theta, gE.contiguous(), gB.contiguous(), ctx.recompute)
-            return torch.from_numpy(grad), gE0, gB0, None, None
+            # dL/dtheta is accumulated in FP64 on the host; autograd wants it
+            # with theta's own dtype and device
+            dtype, device = ctx.theta_meta
+            return torch.from_numpy(grad).to(dtype=dtype, device=device), gE0, gB0, None, None
 
     return FieldRun
