@@ -76,3 +76,22 @@ def test_profile_commands_run_committed_files():
         if words[0] == "ncu" and "-i" not in words:
             assert "--clock-control" in words and words[words.index("--clock-control") + 1] == "none", (name, cmd)
     assert seen_bench >= 5
+
+
+def test_resource_summary_matches_the_sources():
+    """The ptxas table in profiles/ptxas_resources_sm103a.md is what its quoted
+    command prints for the sources as committed (registers, spills, stack and
+    shared memory of every listed kernel): a kernel change that moves them, or
+    a template change that drops a kernel from the pattern, shows here."""
+    import shlex
+    from paper_1907_13088_gb300 import build
+
+    cmd = [c for n, c in _commands() if n == "ptxas_resources_sm103a.md" and "--resources" in c]
+    assert len(cmd) == 1, cmd
+    args = shlex.split(cmd[0])
+    pattern = args[args.index("--resources") + 1]
+    with open(os.path.join(ROOT, "profiles", "ptxas_resources_sm103a.md")) as f:
+        committed = [line for line in f.read().splitlines() if line.startswith("| `")]
+    now = [line for line in build.resources(pattern).splitlines() if line.startswith("| `")]
+    assert any("k_pol2d<0, 4, 3, true, 128, true>" in line for line in now)  # the 4096^2 TE kernel is listed
+    assert now == committed
